@@ -1,0 +1,344 @@
+#!/usr/bin/env python3
+"""Throughput of the flip Monte Carlo sweep on GB300.
+
+A step is `--sweeps-per-step` sweeps of the whole hot path (cell-list build,
+8 checkerboard colour phases with translation and flip attempts, Metropolis,
+commit, per-sweep energy bookkeeping) followed by one FP64 total-energy
+recompute, over one synthetic configuration resident in HBM.  `value` is
+attempted MC moves per second over all ranks; site-pair evaluations per second
+and their fraction of the FP32 peak are reported next to it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl native|reference]
+
+N > 1 runs under torch.distributed.run, one independent replica set per GPU
+(no data-path collective: replicas do not interact).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2506_21290_gb300 import workloads as W  # noqa: E402
+
+METRIC = "MC attempted moves/sec and site-pair evals/sec (frac. FP32 peak), FP32 vs FP64"
+UNIT = "attempted moves/s"
+FLOPS_PER_PAIR_EVAL = 8      # 3 coordinate differences + r^2 (3 mul, 2 add)
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ = 2070.0
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default="single-1000", choices=sorted(W.WORKLOADS))
+    ap.add_argument("--sweeps-per-step", type=int, default=0, help="0: workload default")
+    ap.add_argument("--precision", default="", choices=["", "fp32", "fp64"])
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+DEFAULT_SPS = {"tiny-64": 100, "single-1000": 100, "single-8000": 20, "batched-256": 5, "large-64000": 5}
+
+
+def make_workload(name, rank=0):
+    spec = W.WORKLOADS[name]
+    if "R" in spec:
+        Ms, Ts = W.replica_mix(spec["R"], seed=spec["seed"])
+        Ls = np.array([W.box_length(int(M)) for M in Ms])
+        xyz, ts = [], []
+        for k, M in enumerate(Ms):
+            x, t = W.lattice_start(int(M), Ls[k], k)
+            xyz.append(x)
+            ts.append(t)
+        seeds = np.arange(len(Ms), dtype=np.uint64) + np.uint64(1000 * rank)
+        return dict(L=Ls, n_mol=Ms.astype(np.int32), xyz=np.concatenate(xyz), types=np.concatenate(ts), T=Ts,
+                    seeds=seeds, M_total=int(Ms.sum()), replicas=len(Ms), precision=spec["precision"])
+    M = spec["M"]
+    L = W.box_length(M)
+    xyz, t = W.lattice_start(M, L, spec["seed"])
+    return dict(L=L, n_mol=None, xyz=xyz, types=t, T=spec["T"], seeds=spec["seed"] + 1000 * rank, M_total=M,
+                replicas=1, precision=spec["precision"])
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(device_index)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(wl, name, budget_s, T, mix):
+    """The oracle, as it stands, single-threaded on this host, on a bounded sample."""
+    import oracle
+    oracle.build()
+    if wl["replicas"] > 1:
+        L0, M0 = float(wl["L"][0]), int(wl["n_mol"][0])
+        xyz0, t0 = wl["xyz"][: 3 * M0], wl["types"][: 3 * M0]
+        T0 = float(wl["T"][0])
+        sample_name = "replica 0 of the batch (%d molecules)" % M0
+    else:
+        L0, M0, xyz0, t0, T0 = wl["L"], wl["M_total"], wl["xyz"], wl["types"], T
+        sample_name = "%d molecules" % M0
+    nc = 2
+    while math.floor(2 ** 32 / (nc + 2)) * L0 / 2 ** 32 >= 1.575:
+        nc += 2
+    ch = oracle.Chain(L0, xyz0, t0, W.PAPER_POT, nc=nc)
+    t0w = time.perf_counter()
+    ch.run(1, T0, mix, seed=1)
+    one = time.perf_counter() - t0w
+    n = max(1, int(budget_s / max(one, 1e-6)))
+    t1 = time.perf_counter()
+    ch.run(n, T0, mix, seed=1)
+    dt = time.perf_counter() - t1
+    return {"value": 3 * M0 * n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d sweeps of %s (%s), FP64, O(N) Delta E per move, after 1 untimed sweep"
+                      % (n, sample_name, name)}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    wl = make_workload(args.workload)
+    T = wl["T"] if wl["replicas"] == 1 else float(wl["T"][0])
+    import oracle
+    oracle.build()
+    if wl["replicas"] > 1:
+        M0 = int(wl["n_mol"][0])
+        L0, xyz0, t0 = float(wl["L"][0]), wl["xyz"][: 3 * M0], wl["types"][: 3 * M0]
+        sample = "one sweep of replica 0 (%d molecules) per step" % M0
+    else:
+        M0, L0, xyz0, t0 = wl["M_total"], wl["L"], wl["xyz"], wl["types"]
+        sample = "one sweep of %d molecules per step" % M0
+    nc = 2
+    while math.floor(2 ** 32 / (nc + 2)) * L0 / 2 ** 32 >= 1.575:
+        nc += 2
+    ch = oracle.Chain(L0, xyz0, t0, W.PAPER_POT, nc=nc)
+    for _ in range(args.warmup):
+        ch.run(1, T, W.PAPER_MIX, seed=1)
+    t1 = time.perf_counter()
+    for _ in range(args.steps):
+        ch.run(1, T, W.PAPER_MIX, seed=1)
+    dt = time.perf_counter() - t1
+    v = 3 * M0 * args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "molecules": M0, "T": T, "sweeps_per_step": 1,
+                       "move_mix": "atom 0.8 / flip 0.2"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_native(args):
+    import torch
+    from paper_2506_21290_gb300 import build as B
+    from paper_2506_21290_gb300 import flipmc as F
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        B.build()
+    if dist is not None:
+        dist.barrier()
+    F.load()
+
+    wl = make_workload(args.workload, rank)
+    precision = args.precision or wl["precision"]
+    sps = args.sweeps_per_step or DEFAULT_SPS[args.workload]
+    mix = W.PAPER_MIX
+    h = F.Handle(wl["L"], wl["xyz"], wl["types"], W.PAPER_POT, precision=precision, device=local, n_mol=wl["n_mol"])
+    N = h.N
+    stream = torch.cuda.current_stream()
+    h.set_stream(stream.cuda_stream)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    e_dev = torch.zeros(h.n_rep, dtype=torch.float64, device="cuda")
+
+    def step():
+        h.sweep(sps, wl["T"], mix, wl["seeds"])
+        h.energy_device(e_dev.data_ptr())
+
+    for _ in range(args.warmup):
+        step()
+    h.sync()
+    torch.cuda.synchronize()
+    st0 = h.stats()
+    clocks = Clocks(torch.cuda.current_device())
+    time.sleep(0.4)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    evs = []
+    for _ in range(args.steps):
+        flush.fill_(1)                 # evict the state from L2 between timed steps
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step()
+        b.record(stream)
+        evs.append((a, b))
+    torch.cuda.synchronize()
+    h.sync()
+    clk = clocks.stop()
+    ms = sum(a.elapsed_time(b) for a, b in evs)
+    st1 = h.stats()
+    attempts = sum(sum(s1["attempts"]) - sum(s0["attempts"]) for s0, s1 in zip(st0, st1))
+    pairs = sum(s1["pair_evals"] - s0["pair_evals"] for s0, s1 in zip(st0, st1))
+    rechecks = sum(s1["fp64_rechecks"] - s0["fp64_rechecks"] for s0, s1 in zip(st0, st1))
+    accepts = [sum(s1["accepts"][k] - s0["accepts"][k] for s0, s1 in zip(st0, st1)) for k in range(4)]
+    att_k = [sum(s1["attempts"][k] - s0["attempts"][k] for s0, s1 in zip(st0, st1)) for k in range(4)]
+    geom = sum(s1["rejected_geometry"] - s0["rejected_geometry"] for s0, s1 in zip(st0, st1))
+    tot = torch.tensor([ms, float(attempts), float(pairs)], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        mx = tot.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        sm = tot.clone()
+        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+        ms_max, attempts_all, pairs_all = float(mx[0]), float(sm[1]), float(sm[2])
+    else:
+        ms_max, attempts_all, pairs_all = ms, float(attempts), float(pairs)
+    value = attempts_all / (ms_max / 1000.0)
+    pair_rate = pairs_all / (ms_max / 1000.0)
+
+    # per-kernel durations for the roofline: CUDA events around each stage
+    n_prof = max(2, min(20, sps))
+    st2 = h.stats()
+    stage_ms = h.sweep_timed(n_prof, wl["T"], mix, wl["seeds"])
+    st3 = h.stats()
+    prof_pairs = sum(s3["pair_evals"] - s2["pair_evals"] for s2, s3 in zip(st2, st3))
+    phase_launch_ms = stage_ms[1] / (8 * n_prof)
+    flops_per_launch = FLOPS_PER_PAIR_EVAL * prof_pairs / (8 * n_prof)
+    achieved = flops_per_launch / (phase_launch_ms / 1000.0) / 1e12
+    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    peak_at_clock = (SM_COUNT * FP32_LANES_PER_SM * 2 * clk["sm_mhz"] * 1e6 / 1e12) if clk.get("sm_mhz") else None
+
+    # end to end through the C ABI with host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        h.set_stream(0)
+        torch.cuda.synchronize()
+        xyz_h, t_h = wl["xyz"], wl["types"]
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            h.set_state(xyz_h, t_h)
+            h.sweep(sps, wl["T"], mix, wl["seeds"])
+            E = h.energy()
+            xyz_o, t_o, _s = h.state()
+        dt = time.perf_counter() - t0
+        e2e = {"value": N * sps * args.e2e_steps / dt, "unit": UNIT,
+               "h2d_bytes_per_step": int(16 * N), "d2h_bytes_per_step": int(28 * N + 8 * h.n_rep + 136 * h.n_rep),
+               "steps": args.e2e_steps,
+               "path": "mc_set_state (host positions) + mc_sweep + mc_energy + mc_state (host positions)"}
+
+    if rank != 0:
+        if dist is not None:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        cpu = cpu_baseline(wl, args.workload, args.cpu_seconds, wl["T"] if wl["replicas"] == 1 else None, mix)
+    launches_per_sweep = 4 + 8 + 1
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if precision == "fp32" else "f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "molecules": wl["M_total"], "sites": N, "replicas": wl["replicas"],
+                   "T": wl["T"] if wl["replicas"] == 1 else "uniform [0.75, 3.0] per replica",
+                   "density": W.RHO, "sweeps_per_step": sps, "precision": precision,
+                   "move_mix": "atom translation 0.8 (d=0.1) / flip 0.2",
+                   "start": "simple-cubic lattice, random orientations, then %d warm-up steps" % args.warmup,
+                   "l2": "256 MiB buffer written between timed steps",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "pair_evals_per_s": pair_rate,
+        "pair_evals_fp32_peak_frac": pair_rate * FLOPS_PER_PAIR_EVAL / (peak * 1e12),
+        "fp64_recheck_rate": rechecks / max(attempts, 1),
+        "acceptance": [accepts[k] / att_k[k] if att_k[k] else None for k in range(4)],
+        "geometry_reject_rate": geom / max(attempts, 1),
+        "roofline": {"bound": "alu", "kernel": "phase_kernel<FP32>" if precision == "fp32" else "phase_kernel<FP64>",
+                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": None, "peak_basis": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (max clock)",
+                     "peak_at_measured_clock": peak_at_clock,
+                     "launch_ms": phase_launch_ms, "flops_per_launch": flops_per_launch,
+                     "stage_ms_per_sweep": [x / n_prof for x in stage_ms]},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": args.steps * (sps * launches_per_sweep + 2),
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,288 @@
+/*
+ * flipmc.h -- C ABI of a GB300 (sm_103a) flip Monte Carlo library for the
+ * triangular three-site molecular glass-former of arXiv 2506.21290
+ * ("Molecular motion at the experimental glass transition", Sec. II).
+ *
+ * Model (Sec. II.A).  M molecules of three atoms; atom (site) i belongs to
+ * molecule i/3.  Types 0=A, 1=B, 2=C with diameters sigma_A, sigma_B, sigma_C
+ * (paper: 0.9, 1, 1.1).  Every pair, intra- and intermolecular, interacts by
+ * the WCA potential of Eq. 1 with sigma_ab = (sigma_a + sigma_b)/2 and cutoff
+ * 2^(1/6) sigma_ab; the three bonds of a molecule add the FENE potential of
+ * Eq. 2, -K eps ln(1 - (r / (R0 sigma_ab))^2) (paper: K = 33.75, R0 = 1.5).
+ * Cubic periodic box of side L.
+ *
+ * Chain (Sec. II.B).  Metropolis moves, N = 3M attempts per sweep (one MC time
+ * step).  Move types: atom translation (uniform in [-d_atom, d_atom]^3), flip
+ * (pick a molecule and one of its three median axes; swap the types of the two
+ * other atoms), and two rigid-body moves the paper does not use (molecule
+ * translation, molecule rotation about the centroid).  Sweeps follow a
+ * checkerboard schedule: a random 32-bit shift of an n_c^3 cell grid per sweep,
+ * 8 colours in order, every cell of a colour updated concurrently, a cell with
+ * n atoms running n attempts; a move that would take an atom out of its cell,
+ * or that writes an atom outside the active cell, is rejected.  Random numbers
+ * are Philox4x32-10 keyed on (seed) and counted on (attempt, cell, sweep), so a
+ * run is reproducible bit for bit and independent of the launch layout.
+ *
+ * Precision.  MC_PREC_FP64 evaluates every Delta E in FP64 with one rounding per
+ * operation, summed in a fixed order (moved atom ascending, then partner index
+ * ascending); it reproduces the library's FP64 reference trajectory exactly.
+ * MC_PREC_FP32 evaluates pair terms in FP32 and takes the Metropolis decision in
+ * FP64: when |dE32 - threshold| is within recheck_gap times the sum of term
+ * magnitudes, Delta E is recomputed in the FP64 order above.  Running and total
+ * energies are FP64 in both modes.
+ *
+ * Conventions.  All functions return 0 (MC_OK) or a negative MC_ERR_* code;
+ * mc_last_error() returns a message for the calling thread's last error.
+ * Pointers named host_* or without a prefix are host memory and are only read
+ * or written during the call; inputs are copied, the caller keeps ownership.
+ * Pointers named dev_* are device memory of the handle's GPU, owned by the
+ * caller.  The library owns the device memory it allocates until
+ * mc_destroy().  Arrays are site-major: xyz[3*i + axis], types[i], molecule
+ * m = sites 3m, 3m+1, 3m+2.  Batched handles concatenate replicas in order.
+ * Work is enqueued on the handle's stream (mc_set_stream); functions that
+ * return data synchronise that stream.  A handle must not be used by two
+ * threads at once.
+ */
+#ifndef FLIPMC_H
+#define FLIPMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MC_OK 0
+#define MC_ERR_INVALID_ARG (-1)   /* a size, pointer or parameter is out of range         */
+#define MC_ERR_BAD_STATE (-2)     /* input state has a broken bond or a non-finite energy */
+#define MC_ERR_CUDA (-3)          /* a CUDA runtime call failed                            */
+#define MC_ERR_TIMEOUT (-4)       /* a bounded device wait gave up                         */
+#define MC_ERR_CELL_OVERFLOW (-5) /* a cell neighbourhood exceeded the staging capacity    */
+#define MC_ERR_NO_DEVICE (-6)     /* no usable CUDA device                                 */
+
+#define MC_PREC_FP64 0
+#define MC_PREC_FP32 1
+
+#define MC_MOVE_ATOM 0
+#define MC_MOVE_FLIP 1
+#define MC_MOVE_MOL_TRANS 2
+#define MC_MOVE_MOL_ROT 3
+
+/* Status of one attempted move in the attempt log. */
+#define MC_ST_EVALUATED 0   /* Delta E computed and Metropolis applied           */
+#define MC_ST_LEFT_CELL 1   /* proposal took an atom out of the active cell      */
+#define MC_ST_BOND_BREAK 2  /* a proposed bond length reached R0 sigma_ab        */
+#define MC_ST_NOT_IN_CELL 3 /* an atom the move writes lies outside the cell     */
+
+typedef struct mc_handle mc_handle;
+
+/* Potential of Eq. 1-2: sigma[type], eps, FENE prefactor K (energy in units of
+ * eps) and FENE range factor R0. */
+typedef struct {
+    double sigma[3];
+    double eps;
+    double fene_k;
+    double fene_r0;
+} mc_params;
+
+/* Move mix: probabilities p[MC_MOVE_*] (non-negative, summing to 1 within
+ * 1e-9), atom step half-width d_atom, molecule step half-width d_mol (length
+ * units), and rot_a: the rotation quaternion is (1, rot_a v)/|.| with v
+ * uniform in (-1,1)^3.  Paper mix: p = {0.8, 0.2, 0, 0}. */
+typedef struct {
+    double p[4];
+    double d_atom;
+    double d_mol;
+    double rot_a;
+} mc_move_mix;
+
+/* Creation options.  precision: MC_PREC_FP64 or MC_PREC_FP32.  n_cells: cells
+ * per axis (even, >= 2), 0 picks the largest even n_c whose cell side is at
+ * least R0 * max bonded sigma_ab (the longest possible interaction).
+ * recheck_gap: FP32 decision margin (0 picks 1e-4).  device: CUDA device
+ * ordinal.  stencil_cap: atoms staged per cell neighbourhood (0 = automatic). */
+typedef struct {
+    int precision;
+    int n_cells;
+    int device;
+    int stencil_cap;
+    double recheck_gap;
+} mc_options;
+
+/* Per-replica counters since creation (or mc_reset_stats). */
+typedef struct {
+    uint64_t attempts[4];
+    uint64_t accepts[4];
+    uint64_t rejected_geometry; /* MC_ST_LEFT_CELL + MC_ST_NOT_IN_CELL          */
+    uint64_t rejected_bond;     /* MC_ST_BOND_BREAK                              */
+    uint64_t pair_evals;        /* candidate distances evaluated (old and new)   */
+    uint64_t fp64_rechecks;     /* FP32 mode: decisions retaken in FP64          */
+    uint64_t sweeps;
+    double e_run;               /* running FP64 energy: initial + sum of accepted dE */
+} mc_stats;
+
+/* Static facts of a handle. */
+typedef struct {
+    int n_rep;
+    int precision;
+    int stencil_cap;
+    int total_sites;
+    int total_cells;
+    int max_cells_per_axis;
+    double recheck_gap;
+} mc_info;
+
+/* One attempted move as recorded by mc_sweep_logged(). */
+typedef struct {
+    int32_t site;      /* site index within its replica                         */
+    int16_t move;      /* MC_MOVE_*                                             */
+    int16_t flags;     /* bit 0: FP32 decision retaken in FP64                  */
+    int32_t status;    /* MC_ST_*                                               */
+    int32_t accepted;  /* 1 if accepted                                         */
+    double dE;         /* Delta E as the mode computed it (FP32 value in FP32)  */
+    double dE64;       /* FP64 Delta E when computed (FP64 mode, or recheck)    */
+    double scale;      /* sum of term magnitudes used for the FP32 margin       */
+} mc_log_entry;
+
+/*
+ * Create a single-replica handle.  L: box side (> 0).  n_mol: molecules (>= 1).
+ * xyz: 9*n_mol positions (any real; wrapped into [0,L) and quantised to 32-bit
+ * fixed point, q = floor(frac(x/L) 2^32)).  types: 3*n_mol values in {0,1,2}.
+ * params/opts: NULL picks the paper's potential and FP32 defaults.
+ * Errors: INVALID_ARG (sizes, types, box smaller than two cells of side
+ * R0*max sigma), BAD_STATE (a bond at or beyond R0 sigma_ab, or a non-finite
+ * energy), NO_DEVICE, CUDA.  Model: Sec. II.A; schedule as described above.
+ */
+int mc_create(mc_handle **out, double L, int n_mol, const double *xyz, const int32_t *types,
+              const mc_params *params, const mc_options *opts);
+
+/*
+ * Create a handle of n_rep independent replicas (the paper runs 10 to 100
+ * independent samples per temperature, Sec. III.B) advanced together.
+ * L[n_rep], n_mol[n_rep]; xyz and types concatenate the replicas in order.
+ * Errors as mc_create.
+ */
+int mc_create_batch(mc_handle **out, int n_rep, const double *L, const int32_t *n_mol, const double *xyz,
+                     const int32_t *types, const mc_params *params, const mc_options *opts);
+
+/* Free all device memory and graphs of the handle.  NULL is ignored. */
+void mc_destroy(mc_handle *h);
+
+/* Enqueue subsequent work on this cudaStream_t (NULL: the handle's own stream). */
+int mc_set_stream(mc_handle *h, void *stream);
+
+/*
+ * Run n_sweeps sweeps (each N = 3M attempts per replica, Sec. II.B) at
+ * temperature T with the given move mix and 64-bit seed; the sweep counter
+ * persists in the handle, so consecutive calls continue one chain.  For a
+ * batched handle T and seed apply to every replica.  Asynchronous: returns
+ * after enqueuing; device-side errors surface at the next synchronising call.
+ * Errors: INVALID_ARG (T <= 0, bad mix, n_sweeps < 0), CUDA.
+ */
+int mc_sweep(mc_handle *h, int n_sweeps, double T, const mc_move_mix *mix, uint64_t seed);
+
+/* Batched variant: T[n_rep] and seeds[n_rep] per replica. */
+int mc_sweep_batch(mc_handle *h, int n_sweeps, const double *T, const mc_move_mix *mix, const uint64_t *seeds);
+
+/*
+ * As mc_sweep, recording every attempt in log_out (host, n_sweeps * total_sites
+ * entries, layout [replica][sweep][slot], slot = cell start + attempt number).
+ * Synchronous.  For tests and audits; slower than mc_sweep.
+ */
+int mc_sweep_logged(mc_handle *h, int n_sweeps, const double *T, const mc_move_mix *mix, const uint64_t *seeds,
+                    mc_log_entry *log_out);
+
+/* Wait for enqueued work; return the first device-side error, if any. */
+int mc_sync(mc_handle *h);
+
+/*
+ * Total energy of each replica, recomputed from the state in FP64 over the
+ * cell neighbourhoods (Eq. 1 + Eq. 2, every pair once): E_out[n_rep].
+ * Synchronous.
+ */
+int mc_energy(mc_handle *h, double *E_out);
+
+/*
+ * As mc_energy, but only enqueued on the handle's stream: dev_E_out is a
+ * device buffer of n_rep doubles owned by the caller (for example a torch
+ * tensor).  No synchronisation; errors surface at the next mc_sync.
+ */
+int mc_energy_device(mc_handle *h, double *dev_E_out);
+
+/*
+ * Run n_sweeps sweeps without graphs, timing each stage with CUDA events on
+ * the handle's stream: ms_out[0] = cell-list build, ms_out[1] = the 8 colour
+ * phases, ms_out[2] = per-sweep finalisation, each the total over the sweeps
+ * in milliseconds.  Same chain as mc_sweep_batch.  Synchronous.  For
+ * measurements; mc_sweep is the production path.
+ */
+int mc_sweep_timed(mc_handle *h, int n_sweeps, const double *T, const mc_move_mix *mix, const uint64_t *seeds,
+                   double *ms_out);
+
+/*
+ * Copy the state out: xyz_out[3*total_sites] (wrapped, x = q L / 2^32),
+ * types_out[total_sites], stats_out[n_rep]; any pointer may be NULL.
+ * Synchronous.
+ */
+int mc_state(mc_handle *h, double *xyz_out, int32_t *types_out, mc_stats *stats_out);
+
+/*
+ * Exact state: q_out[3*total_sites] fixed-point positions, X_out[3*total_sites]
+ * unwrapped fixed point (q + 2^32 * periodic images crossed), types_out.  Any
+ * pointer may be NULL.  Synchronous.
+ */
+int mc_state_fixed(mc_handle *h, uint32_t *q_out, int64_t *X_out, int32_t *types_out);
+
+/*
+ * Replace the state from host arrays (same layout and quantisation as
+ * mc_create).  Stats and the sweep counter are kept; e_run is reset to the new
+ * total energy; image counters are cleared.  Errors as mc_create.
+ */
+int mc_set_state(mc_handle *h, const double *xyz, const int32_t *types);
+
+/*
+ * Exact restore (checkpoint resume): q[3*total_sites] fixed-point positions,
+ * X[3*total_sites] unwrapped fixed point or NULL (image counters restored from
+ * (X - q) / 2^32, else cleared), types[total_sites].  Same checks and
+ * e_run reset as mc_set_state.
+ */
+int mc_set_state_fixed(mc_handle *h, const uint32_t *q, const int64_t *X, const int32_t *types);
+
+/* Set the sweep counter (checkpoint resume).  Random numbers depend only on
+ * (seed, sweep, cell, attempt), so resuming reproduces an uninterrupted run. */
+int mc_set_sweep(mc_handle *h, uint64_t sweep);
+
+/* Clear the counters of mc_stats (not e_run). */
+int mc_reset_stats(mc_handle *h);
+
+/*
+ * Record the time origin of the correlation functions (Sec. III.B): the
+ * unwrapped positions, and per molecule the reference atom k (the atom of
+ * type B now; Eq. 7) and the orientation vector u(0) from the centroid to k.
+ */
+int mc_set_t0(mc_handle *h);
+
+/*
+ * Time correlations against the last mc_set_t0 (Sec. III.B, Eq. 5-7):
+ * out[3*r + 0] = F_s(q,t) over atoms and the n_qa wavevectors qvec_atom[3*n_qa],
+ * out[3*r + 1] = F_s^cm over molecules and the n_qc vectors qvec_cm,
+ * out[3*r + 2] = C_2(t) = <P_2(u(t).u(0))>.
+ * Optional per-particle outputs (NULL to skip): fs_atom[total_sites],
+ * fscm_mol[total_mol], c2_mol[total_mol].  FP64.  Synchronous.
+ * Errors: INVALID_ARG (no t0, n_q < 1 or > 256).
+ */
+int mc_observables(mc_handle *h, const double *qvec_atom, int n_qa, const double *qvec_cm, int n_qc,
+                   double *out, double *fs_atom, double *fscm_mol, double *c2_mol);
+
+/* Static facts of the handle. */
+int mc_get_info(mc_handle *h, mc_info *info);
+
+/* Message describing the calling thread's last error ("" if none). */
+const char *mc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FLIPMC_H */

@@ -1,0 +1,184 @@
+// Total energy (Eq. 1 + Eq. 2, FP64) over the cell neighbourhoods, and the
+// time correlations of Sec. III.B (Eq. 5-7).
+#include "cell_list.h"
+#include "energy.h"
+#include "flipmc_device.cuh"
+
+namespace flipmc {
+
+// Energy of every atom i with its partners j > i (site index) in the 27 (or 8)
+// neighbour cells; pairs beyond every cutoff are screened in FP32 and add 0.
+__global__ void energy_sites_kernel(DevState d, int buf, double *e_site)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= d.n_sites) return;
+    const int r = d.rep_of_site[g];
+    const RepInfo ri = d.rep[r];
+    const ModelDev &md = *d.model;
+    const int4 me = d.rec[buf][g];
+    const int si = rec_site(me.w), ti = rec_type(me.w), mi = rec_mol(me.w);
+    const int nc = ri.nc;
+    const uint32_t *shift = d.ctr[r].shift;
+    const int cx = (int)cell_axis((uint32_t)me.x, shift[0], nc);
+    const int cy = (int)cell_axis((uint32_t)me.y, shift[1], nc);
+    const int cz = (int)cell_axis((uint32_t)me.z, shift[2], nc);
+    float rc2max = 0.f;
+    for (int k = 0; k < 9; ++k) rc2max = fmaxf(rc2max, md.rc2f[k]);
+    const float pre = rc2max * 1.01f;
+    const bool small = nc == 2;
+    const int ns = small ? 8 : 27;
+    double e = 0.0;
+    for (int k = 0; k < ns; ++k) {
+        int ox, oy, oz;
+        if (small) {
+            ox = k & 1; oy = (k >> 1) & 1; oz = k >> 2;
+        } else {
+            ox = k % 3 - 1; oy = (k / 3) % 3 - 1; oz = k / 9 - 1;
+        }
+        const int c = ri.cell_off + (((cz + oz + nc) % nc) * nc + (cy + oy + nc) % nc) * nc + (cx + ox + nc) % nc;
+        const int s0 = d.cell_start[c], s1 = d.cell_start[c + 1];
+        for (int j = s0; j < s1; ++j) {
+            const int4 o = d.rec[buf][j];
+            const int sj = rec_site(o.w);
+            if (sj <= si) continue;
+            const int dx = (int)((uint32_t)o.x - (uint32_t)me.x);
+            const int dy = (int)((uint32_t)o.y - (uint32_t)me.y);
+            const int dz = (int)((uint32_t)o.z - (uint32_t)me.z);
+            const bool bonded = rec_mol(o.w) == mi;
+            if (!bonded) {
+                const float fx = (float)dx * ri.hf, fy = (float)dy * ri.hf, fz = (float)dz * ri.hf;
+                if (fx * fx + fy * fy + fz * fz > pre) continue;
+            }
+            const double r2 = r2_fixed64(dx, dy, dz, ri.h);
+            e = __dadd_rn(e, phi64(md, r2, 3 * ti + rec_type(o.w), bonded));
+        }
+    }
+    e_site[ri.site_off + si] = e;
+}
+
+// Fixed-order sum of a per-site (or per-molecule) array over each replica.
+__global__ void __launch_bounds__(256) replica_sum_kernel(DevState d, const double *v, int per_mol, double scale_inv_n,
+                                                          double *out, int stride, int offset)
+{
+    const int r = blockIdx.x;
+    const RepInfo ri = d.rep[r];
+    const int n = per_mol ? ri.n_sites / 3 : ri.n_sites;
+    const int off = per_mol ? ri.site_off / 3 : ri.site_off;
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += 256) s = __dadd_rn(s, v[off + i]);
+    __shared__ double red[256];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] = __dadd_rn(red[threadIdx.x], red[threadIdx.x + w]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[(size_t)r * stride + offset] = scale_inv_n != 0.0 ? red[0] / (double)n : red[0];
+}
+
+void launch_energy(const DevState &d, int buf, double *e_site, double *e_out_dev, cudaStream_t st)
+{
+    energy_sites_kernel<<<(d.n_sites + 255) / 256, 256, 0, st>>>(d, buf, e_site);
+    replica_sum_kernel<<<d.n_rep, 256, 0, st>>>(d, e_site, 0, 0.0, e_out_dev, 1, 0);
+}
+
+// Unwrapped fixed-point positions and types in site-index order.
+__global__ void gather_kernel(DevState d, int buf, long long *X, int *types)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= d.n_sites) return;
+    const int r = d.rep_of_site[g];
+    const int off = d.rep[r].site_off;
+    const int4 rc = d.rec[buf][g];
+    const int s = off + rec_site(rc.w);
+    X[3 * s + 0] = (long long)(uint32_t)rc.x + ((long long)d.img[3 * s + 0] << 32);
+    X[3 * s + 1] = (long long)(uint32_t)rc.y + ((long long)d.img[3 * s + 1] << 32);
+    X[3 * s + 2] = (long long)(uint32_t)rc.z + ((long long)d.img[3 * s + 2] << 32);
+    types[s] = rec_type(rc.w);
+}
+
+// Orientation of molecule m (global index): centroid -> site kref, from the
+// wrapped positions with intramolecular minimum images (equal masses).
+__device__ void orientation(const long long *X, int m, int kref, double h, double *u)
+{
+    const long long *x0 = X + 9 * (size_t)m;
+    double rel[3][3];
+    for (int k = 0; k < 3; ++k)
+        for (int ax = 0; ax < 3; ++ax) rel[k][ax] = (double)(int)((uint32_t)x0[3 * k + ax] - (uint32_t)x0[ax]) * h;
+    double n2 = 0.0;
+    for (int ax = 0; ax < 3; ++ax) {
+        const double cm = ((rel[0][ax] + rel[1][ax]) + rel[2][ax]) / 3.0;
+        u[ax] = rel[kref][ax] - cm;
+        n2 += u[ax] * u[ax];
+    }
+    const double inv = 1.0 / sqrt(n2);
+    for (int ax = 0; ax < 3; ++ax) u[ax] *= inv;
+}
+
+__global__ void set_t0_kernel(DevState d, const long long *X, const int *types, ObsState o)
+{
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= d.n_sites / 3) return;
+    for (int k = 0; k < 9; ++k) o.X0[9 * (size_t)m + k] = X[9 * (size_t)m + k];
+    int kref = 0;
+    for (int s = 2; s >= 0; --s)
+        if (types[3 * m + s] == 1) kref = s;
+    o.kref[m] = kref;
+    const int r = d.rep_of_site[3 * m];
+    double u[3];
+    orientation(X, m, kref, d.rep[r].h, u);
+    for (int ax = 0; ax < 3; ++ax) o.u0[3 * (size_t)m + ax] = u[ax];
+}
+
+// Per molecule: F_s of its three atoms, F_s^cm and C_2 (Eq. 5-7).
+__global__ void observables_kernel(DevState d, const long long *X, ObsState o, const double *qa, int nqa,
+                                   const double *qc, int nqc, double *fs_site, double *fscm_mol, double *c2_mol)
+{
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= d.n_sites / 3) return;
+    const int r = d.rep_of_site[3 * m];
+    const double h = d.rep[r].h;
+    double dx[3][3];
+    for (int k = 0; k < 3; ++k)
+        for (int ax = 0; ax < 3; ++ax)
+            dx[k][ax] = (double)(X[9 * (size_t)m + 3 * k + ax] - o.X0[9 * (size_t)m + 3 * k + ax]) * h;
+    for (int k = 0; k < 3; ++k) {
+        double s = 0.0;
+        for (int q = 0; q < nqa; ++q)
+            s += cos(qa[3 * q] * dx[k][0] + qa[3 * q + 1] * dx[k][1] + qa[3 * q + 2] * dx[k][2]);
+        fs_site[3 * (size_t)m + k] = s / (double)nqa;
+    }
+    double cm[3];
+    for (int ax = 0; ax < 3; ++ax) cm[ax] = ((dx[0][ax] + dx[1][ax]) + dx[2][ax]) / 3.0;
+    double s = 0.0;
+    for (int q = 0; q < nqc; ++q) s += cos(qc[3 * q] * cm[0] + qc[3 * q + 1] * cm[1] + qc[3 * q + 2] * cm[2]);
+    fscm_mol[m] = s / (double)nqc;
+    double u[3];
+    orientation(X, m, o.kref[m], h, u);
+    const double x = u[0] * o.u0[3 * (size_t)m] + u[1] * o.u0[3 * (size_t)m + 1] + u[2] * o.u0[3 * (size_t)m + 2];
+    c2_mol[m] = 1.5 * x * x - 0.5;
+}
+
+void launch_gather(const DevState &d, int buf, long long *X, int *types, cudaStream_t st)
+{
+    gather_kernel<<<(d.n_sites + 255) / 256, 256, 0, st>>>(d, buf, X, types);
+}
+
+void launch_set_t0(const DevState &d, const long long *X, const int *types, const ObsState &o, cudaStream_t st)
+{
+    const int nm = d.n_sites / 3;
+    set_t0_kernel<<<(nm + 127) / 128, 128, 0, st>>>(d, X, types, o);
+}
+
+void launch_observables(const DevState &d, const long long *X, const ObsState &o, const double *qa, int nqa,
+                        const double *qc, int nqc, double *fs_site, double *fscm_mol, double *c2_mol, double *out,
+                        cudaStream_t st)
+{
+    const int nm = d.n_sites / 3;
+    observables_kernel<<<(nm + 127) / 128, 128, 0, st>>>(d, X, o, qa, nqa, qc, nqc, fs_site, fscm_mol, c2_mol);
+    replica_sum_kernel<<<d.n_rep, 256, 0, st>>>(d, fs_site, 0, 1.0, out, 3, 0);
+    replica_sum_kernel<<<d.n_rep, 256, 0, st>>>(d, fscm_mol, 1, 1.0, out, 3, 1);
+    replica_sum_kernel<<<d.n_rep, 256, 0, st>>>(d, c2_mol, 1, 1.0, out, 3, 2);
+}
+
+}  // namespace flipmc

@@ -1,0 +1,920 @@
+// Host engine behind the C ABI of include/flipmc.h.
+//
+// A handle owns all device memory of one batch of replicas (a single replica
+// is a batch of one).  State lives on the device as cell-sorted 16-byte
+// records {qx, qy, qz, w}, w = (molecule << 4) | (slot << 2) | type, in two
+// buffers: each sweep's cell-list build reads one and writes the other.  One
+// sweep (cell list + 8 colour phases + finalisation) is captured once per
+// buffer parity as a CUDA graph and replayed; everything a sweep reads that can
+// change between calls (T, seed, move mix, sweep counter) sits in device
+// memory, so the graphs never need re-capture.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/flipmc.h"
+#include "cell_list.h"
+#include "energy.h"
+#include "flipmc_types.h"
+
+using namespace flipmc;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string &msg)
+{
+    g_err = msg;
+    return code;
+}
+
+#define CUDA_TRY(expr)                                                                              \
+    do {                                                                                            \
+        cudaError_t _e = (expr);                                                                    \
+        if (_e != cudaSuccess)                                                                      \
+            return fail(MC_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(_e));           \
+    } while (0)
+
+const double kCbrt2 = 0x1.428a2f98d728bp+0;   // double nearest 2^(1/3)
+const double kTwo32 = 4294967296.0;
+
+// x -> floor(frac(x / L) * 2^32), the library's quantisation of positions
+uint32_t quantize(double x, double L)
+{
+    double t = x / L;
+    t = t - std::floor(t);
+    double v = std::floor(t * kTwo32);
+    if (v >= kTwo32) v = 0.0;
+    return (uint32_t)v;
+}
+
+struct Buf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace
+
+struct mc_handle {
+    int device = 0;
+    int precision = MC_PREC_FP32;
+    int n_rep = 0;
+    int n_sites = 0;
+    int n_cells = 0;
+    int n_act = 0;
+    int stencil_cap = 0;
+    int wpb = 4;
+    double recheck_gap = 1e-4;
+    mc_params params{};
+    std::vector<RepInfo> reps;
+    std::vector<int> mol_off;
+    cudaStream_t own_stream = nullptr;
+    cudaStream_t stream = nullptr;
+    int cur = 0;
+    bool has_t0 = false;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    DevState ds{};
+    ObsState obs{};
+    std::vector<Buf> allocs;
+    // device scratch
+    RepInfo *d_rep = nullptr;
+    RepParam *d_par = nullptr;
+    RepCtr *d_ctr = nullptr;
+    ModelDev *d_model = nullptr;
+    MixDev *d_mix = nullptr;
+    int *d_rep_of_site = nullptr;
+    int *d_act_off = nullptr;
+    double *d_e_site = nullptr;
+    double *d_e_out = nullptr;
+    long long *d_X = nullptr;
+    int *d_types = nullptr;
+    double *d_fs = nullptr, *d_fscm = nullptr, *d_c2 = nullptr, *d_q = nullptr, *d_obs_out = nullptr;
+    std::vector<RepParam> par_host;
+    std::vector<RepParam> par_sent;
+    MixDev mix_sent{};
+    bool params_valid = false;
+    ModelDev model_host{};
+
+    template <class T>
+    int alloc(T **p, size_t n)
+    {
+        void *q = nullptr;
+        const size_t bytes = std::max<size_t>(n, 1) * sizeof(T);
+        cudaError_t e = cudaMalloc(&q, bytes);
+        if (e != cudaSuccess) return fail(MC_ERR_CUDA, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        cudaMemset(q, 0, bytes);
+        allocs.push_back({q, bytes});
+        *p = (T *)q;
+        return MC_OK;
+    }
+};
+
+namespace {
+
+int set_device(const mc_handle *h)
+{
+    CUDA_TRY(cudaSetDevice(h->device));
+    return MC_OK;
+}
+
+void default_params(mc_params *p)
+{
+    p->sigma[0] = 0.9;
+    p->sigma[1] = 1.0;
+    p->sigma[2] = 1.1;
+    p->eps = 1.0;
+    p->fene_k = 33.75;
+    p->fene_r0 = 1.5;
+}
+
+void build_model(const mc_params &p, double gap, ModelDev &md)
+{
+    std::memset(&md, 0, sizeof md);
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            const int ab = 3 * a + b;
+            const double s = (p.sigma[a] + p.sigma[b]) * 0.5;
+            const double s2 = s * s;
+            const double R = p.fene_r0 * s;
+            md.s2[ab] = s2;
+            md.rc2[ab] = kCbrt2 * s2;
+            md.R2[ab] = R * R;
+            md.s2f[ab] = (float)md.s2[ab];
+            md.rc2f[ab] = (float)md.rc2[ab];
+            md.R2f[ab] = (float)md.R2[ab];
+            md.invR2f[ab] = (float)(1.0 / md.R2[ab]);
+        }
+    md.eps = p.eps;
+    md.e4 = 4.0 * p.eps;
+    md.ke = p.fene_k * p.eps;
+    md.nke = -md.ke;
+    md.epsf = (float)md.eps;
+    md.e4f = (float)md.e4;
+    md.kef = (float)md.ke;
+    md.nkef = (float)md.nke;
+    md.bond_guard_f = 0.995f;
+    md.recheck_gap_f = (float)gap;
+}
+
+// Longest interaction range: the WCA cutoff of any type pair, and the FENE
+// divergence of any pair that can form a bond (type pairs inside a molecule's
+// multiset, which flips permute but never change).
+double interaction_range(const mc_params &p, const int32_t *types, int n_mol)
+{
+    double smax = 0.0;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) smax = std::max(smax, 0.5 * (p.sigma[a] + p.sigma[b]));
+    double range = std::pow(2.0, 1.0 / 6.0) * smax;
+    bool seen[3][3] = {};
+    for (int m = 0; m < n_mol; ++m)
+        for (int k = 0; k < 3; ++k)
+            for (int l = k + 1; l < 3; ++l) seen[types[3 * m + k]][types[3 * m + l]] = true;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b)
+            if (seen[a][b]) range = std::max(range, p.fene_r0 * 0.5 * (p.sigma[a] + p.sigma[b]));
+    return range;
+}
+
+// smallest cell width in length units for n_c cells per axis
+double min_cell_width(double L, int nc)
+{
+    return std::floor(kTwo32 / nc) * (L / kTwo32);
+}
+
+int choose_cells(double L, double range, int request, int *nc_out)
+{
+    if (L < 2.0 * range) return fail(MC_ERR_INVALID_ARG, "box side smaller than twice the interaction range");
+    if (request > 0) {
+        if (request % 2 != 0 || request < 2) return fail(MC_ERR_INVALID_ARG, "n_cells must be even and >= 2");
+        if (min_cell_width(L, request) < range)
+            return fail(MC_ERR_INVALID_ARG, "n_cells makes cells narrower than the interaction range");
+        *nc_out = request;
+        return MC_OK;
+    }
+    int nc = 2;
+    while (min_cell_width(L, nc + 2) >= range && nc + 2 <= 1024) nc += 2;
+    *nc_out = nc;
+    return MC_OK;
+}
+
+int check_mix(const mc_move_mix *mx)
+{
+    if (!mx) return fail(MC_ERR_INVALID_ARG, "mix is NULL");
+    double s = 0.0;
+    for (int k = 0; k < 4; ++k) {
+        if (!(mx->p[k] >= 0.0) || !std::isfinite(mx->p[k])) return fail(MC_ERR_INVALID_ARG, "mix probability < 0");
+        s += mx->p[k];
+    }
+    if (std::fabs(s - 1.0) > 1e-9) return fail(MC_ERR_INVALID_ARG, "mix probabilities do not sum to 1");
+    if (!(mx->d_atom >= 0.0) || !(mx->d_mol >= 0.0) || !(mx->rot_a >= 0.0) || !std::isfinite(mx->rot_a))
+        return fail(MC_ERR_INVALID_ARG, "negative or non-finite step width");
+    return MC_OK;
+}
+
+// thresholds on a 32-bit word from cumulative probabilities; a threshold past
+// which only zero-probability types remain is 2^32
+void mix_thresholds(const mc_move_mix *mx, uint64_t thr[3])
+{
+    double c = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        c = c + mx->p[k];
+        bool tail_zero = true;
+        for (int m = k + 1; m < 4; ++m) tail_zero = tail_zero && (mx->p[m] == 0.0);
+        const double v = std::floor(c * kTwo32);
+        thr[k] = (tail_zero || v >= kTwo32) ? (uint64_t)4294967296ull : (uint64_t)v;
+    }
+}
+
+int32_t fixed_half_width(double d, double L)
+{
+    return (int32_t)std::floor(d / L * kTwo32);
+}
+
+// Quantise (xyz) or take as given (qfix) and pack the records of all replicas
+// (site order); validate bonds.
+int pack_records(mc_handle *h, const double *xyz, const uint32_t *qfix, const int32_t *types, std::vector<int4> &rec)
+{
+    rec.resize(h->n_sites);
+    for (int r = 0; r < h->n_rep; ++r) {
+        const RepInfo &ri = h->reps[r];
+        for (int i = 0; i < ri.n_sites; ++i) {
+            const int g = ri.site_off + i;
+            const int t = types[g];
+            if (t < 0 || t > 2) return fail(MC_ERR_INVALID_ARG, "type outside {0,1,2}");
+            int4 v;
+            if (qfix) {
+                v.x = (int)qfix[3 * (size_t)g + 0];
+                v.y = (int)qfix[3 * (size_t)g + 1];
+                v.z = (int)qfix[3 * (size_t)g + 2];
+            } else {
+                for (int ax = 0; ax < 3; ++ax)
+                    if (!std::isfinite(xyz[3 * (size_t)g + ax])) return fail(MC_ERR_BAD_STATE, "non-finite position");
+                v.x = (int)quantize(xyz[3 * (size_t)g + 0], ri.L);
+                v.y = (int)quantize(xyz[3 * (size_t)g + 1], ri.L);
+                v.z = (int)quantize(xyz[3 * (size_t)g + 2], ri.L);
+            }
+            v.w = ((i / 3) << 4) | ((i % 3) << 2) | t;
+            rec[g] = v;
+        }
+        // every bond strictly inside its FENE range
+        for (int m = 0; m < ri.n_sites / 3; ++m)
+            for (int k = 0; k < 3; ++k)
+                for (int l = k + 1; l < 3; ++l) {
+                    const int4 a = rec[ri.site_off + 3 * m + k], b = rec[ri.site_off + 3 * m + l];
+                    double r2 = 0.0;
+                    const int da[3] = {(int)((uint32_t)b.x - (uint32_t)a.x), (int)((uint32_t)b.y - (uint32_t)a.y),
+                                       (int)((uint32_t)b.z - (uint32_t)a.z)};
+                    for (int ax = 0; ax < 3; ++ax) {
+                        const double x = (double)da[ax] * ri.h;
+                        r2 += x * x;
+                    }
+                    if (!(r2 < h->model_host.R2[3 * (a.w & 3) + (b.w & 3)]))
+                        return fail(MC_ERR_BAD_STATE, "a bond is at or beyond its FENE range (replica " +
+                                                          std::to_string(r) + ", molecule " + std::to_string(m) + ")");
+                }
+    }
+    return MC_OK;
+}
+
+int check_device_errors(mc_handle *h)
+{
+    int e = 0;
+    CUDA_TRY(cudaMemcpyAsync(&e, h->ds.err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    if (e & ERR_STENCIL) return fail(MC_ERR_CELL_OVERFLOW, "a cell neighbourhood exceeded the staging capacity");
+    if (e & ERR_TERMS) return fail(MC_ERR_CELL_OVERFLOW, "too many nonzero FP64 terms in one move");
+    if (e & ERR_TIMEOUT) return fail(MC_ERR_TIMEOUT, "a device wait timed out");
+    return MC_OK;
+}
+
+// energy of each replica into h->d_e_out (device)
+int enqueue_energy(mc_handle *h)
+{
+    launch_energy(h->ds, h->cur, h->d_e_site, h->d_e_out, h->stream);
+    CUDA_TRY(cudaGetLastError());
+    return MC_OK;
+}
+
+int rebuild_and_reset(mc_handle *h, const std::vector<int4> &rec, const std::vector<int> *img = nullptr)
+{
+    // upload in site order into the spare buffer, sort into the other
+    const int spare = h->cur;
+    CUDA_TRY(cudaMemcpyAsync(h->ds.rec[spare], rec.data(), sizeof(int4) * rec.size(), cudaMemcpyHostToDevice,
+                             h->stream));
+    launch_cell_list(h->ds, spare, spare ^ 1, h->stream);
+    h->cur = spare ^ 1;
+    if (img)
+        CUDA_TRY(cudaMemcpyAsync(h->ds.img, img->data(), sizeof(int) * img->size(), cudaMemcpyHostToDevice, h->stream));
+    else
+        CUDA_TRY(cudaMemsetAsync(h->ds.img, 0, sizeof(int) * 3 * (size_t)h->n_sites, h->stream));
+    int rc = enqueue_energy(h);
+    if (rc) return rc;
+    CUDA_TRY(cudaMemcpyAsync(h->ds.e_run, h->d_e_out, sizeof(double) * h->n_rep, cudaMemcpyDeviceToDevice, h->stream));
+    std::vector<double> e(h->n_rep);
+    CUDA_TRY(cudaMemcpyAsync(e.data(), h->d_e_out, sizeof(double) * h->n_rep, cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    rc = check_device_errors(h);
+    if (rc) return rc;
+    for (int r = 0; r < h->n_rep; ++r)
+        if (!std::isfinite(e[r])) return fail(MC_ERR_BAD_STATE, "non-finite energy in replica " + std::to_string(r));
+    h->has_t0 = false;
+    return MC_OK;
+}
+
+int upload_params(mc_handle *h, const double *T, const mc_move_mix *mix, const uint64_t *seeds, bool same_T_seed)
+{
+    for (int r = 0; r < h->n_rep; ++r) {
+        const double t = same_T_seed ? T[0] : T[r];
+        if (!(t > 0.0) || !std::isfinite(t)) return fail(MC_ERR_INVALID_ARG, "temperature must be positive");
+        RepParam &p = h->par_host[r];
+        p.T = t;
+        p.seed = same_T_seed ? seeds[0] : seeds[r];
+        p.D_atom = fixed_half_width(mix->d_atom, h->reps[r].L);
+        p.D_mol = fixed_half_width(mix->d_mol, h->reps[r].L);
+        if (p.D_atom < 0 || p.D_mol < 0 || (double)p.D_atom > 0.25 * kTwo32 || (double)p.D_mol > 0.25 * kTwo32)
+            return fail(MC_ERR_INVALID_ARG, "step width out of range");
+    }
+    MixDev mx{};
+    mix_thresholds(mix, mx.thr);
+    mx.rot_a = mix->rot_a;
+    // identical parameters are not uploaded again, so that consecutive calls
+    // stay asynchronous (a copy from pageable memory waits for the stream)
+    if (h->params_valid && std::memcmp(h->par_sent.data(), h->par_host.data(), sizeof(RepParam) * h->n_rep) == 0 &&
+        std::memcmp(&h->mix_sent, &mx, sizeof(MixDev)) == 0)
+        return MC_OK;
+    CUDA_TRY(cudaMemcpyAsync(h->d_par, h->par_host.data(), sizeof(RepParam) * h->n_rep, cudaMemcpyHostToDevice,
+                             h->stream));
+    CUDA_TRY(cudaMemcpyAsync(h->d_mix, &mx, sizeof(MixDev), cudaMemcpyHostToDevice, h->stream));
+    h->par_sent = h->par_host;
+    h->mix_sent = mx;
+    h->params_valid = true;
+    return MC_OK;
+}
+
+int ensure_graph(mc_handle *h, int buf)
+{
+    if (h->graph[buf]) return MC_OK;
+    cudaStream_t cs;
+    CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t g;
+    CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    launch_cell_list(h->ds, buf, buf ^ 1, cs);
+    LogArgs none{nullptr, 0, 0};
+    launch_phases(h->ds, buf ^ 1, h->wpb, none, cs);
+    cudaError_t e = cudaStreamEndCapture(cs, &g);
+    if (e != cudaSuccess) {
+        cudaStreamDestroy(cs);
+        return fail(MC_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    }
+    e = cudaGraphInstantiate(&h->graph[buf], g, 0);
+    cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) return fail(MC_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    return MC_OK;
+}
+
+int create_impl(mc_handle **out, int n_rep, const double *L, const int32_t *n_mol, const double *xyz,
+                const int32_t *types, const mc_params *params, const mc_options *opts)
+{
+    if (!out) return fail(MC_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (n_rep < 1 || !L || !n_mol || !xyz || !types) return fail(MC_ERR_INVALID_ARG, "NULL input or n_rep < 1");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) return fail(MC_ERR_NO_DEVICE, "no CUDA device");
+    mc_options o{};
+    o.precision = MC_PREC_FP32;
+    if (opts) o = *opts;
+    if (o.precision != MC_PREC_FP32 && o.precision != MC_PREC_FP64) return fail(MC_ERR_INVALID_ARG, "precision");
+    if (o.device < 0 || o.device >= ndev) return fail(MC_ERR_INVALID_ARG, "device ordinal");
+    mc_params p;
+    default_params(&p);
+    if (params) p = *params;
+    for (int k = 0; k < 3; ++k)
+        if (!(p.sigma[k] > 0.0)) return fail(MC_ERR_INVALID_ARG, "sigma must be positive");
+    if (!(p.eps > 0.0) || !(p.fene_k >= 0.0) || !(p.fene_r0 > 0.0)) return fail(MC_ERR_INVALID_ARG, "potential params");
+
+    auto *h = new mc_handle();
+    h->device = o.device;
+    h->precision = o.precision;
+    h->params = p;
+    h->recheck_gap = o.recheck_gap > 0.0 ? o.recheck_gap : 1e-4;
+    h->n_rep = n_rep;
+    build_model(p, h->recheck_gap, h->model_host);
+
+    // layout
+    long long sites = 0, cells = 0, act = 0;
+    double max_stencil = 0.0;
+    std::vector<int> act_off(n_rep + 1, 0), rep_of_site;
+    for (int r = 0; r < n_rep; ++r) {
+        if (n_mol[r] < 1) {
+            delete h;
+            return fail(MC_ERR_INVALID_ARG, "n_mol < 1");
+        }
+        if (!(L[r] > 0.0) || !std::isfinite(L[r])) {
+            delete h;
+            return fail(MC_ERR_INVALID_ARG, "box side must be positive");
+        }
+        const int32_t *tr = types + sites;
+        for (long long i = 0; i < 3LL * n_mol[r]; ++i)
+            if (tr[i] < 0 || tr[i] > 2) {
+                delete h;
+                return fail(MC_ERR_INVALID_ARG, "type outside {0,1,2}");
+            }
+        const double range = interaction_range(p, tr, n_mol[r]);
+        int nc = 0;
+        int rc = choose_cells(L[r], range, o.n_cells, &nc);
+        if (rc) {
+            delete h;
+            return rc;
+        }
+        RepInfo ri{};
+        ri.n_sites = 3 * n_mol[r];
+        ri.site_off = (int)sites;
+        ri.nc = nc;
+        ri.cell_off = (int)cells;
+        ri.act_off = (int)act;
+        ri.L = L[r];
+        ri.h = L[r] / kTwo32;
+        ri.inv_h = kTwo32 / L[r];
+        ri.hf = (float)ri.h;
+        h->reps.push_back(ri);
+        for (int i = 0; i < ri.n_sites; ++i) rep_of_site.push_back(r);
+        sites += ri.n_sites;
+        cells += (long long)nc * nc * nc;
+        act += (long long)(nc / 2) * (nc / 2) * (nc / 2);
+        act_off[r + 1] = (int)act;
+        const double per_cell = (double)ri.n_sites / ((double)nc * nc * nc);
+        const double st = (nc == 2) ? (double)ri.n_sites : 27.0 * per_cell * 1.6 + 64.0;
+        max_stencil = std::max(max_stencil, std::min(st, (double)ri.n_sites));
+        if (sites > (1LL << 30)) {
+            delete h;
+            return fail(MC_ERR_INVALID_ARG, "too many sites");
+        }
+    }
+    h->n_sites = (int)sites;
+    h->n_cells = (int)cells;
+    h->n_act = (int)act;
+    int cap = o.stencil_cap > 0 ? o.stencil_cap : ((int)std::ceil(max_stencil) + 31) / 32 * 32;
+    h->stencil_cap = cap;
+    // warps per block: as many as fit 200 KB of shared memory, at most 4
+    const size_t per_warp = phase_smem_bytes(cap, 1);
+    h->wpb = (int)std::max<size_t>(1, std::min<size_t>(4, (200u * 1024u) / per_warp));
+    if (per_warp > 220u * 1024u) {
+        delete h;
+        return fail(MC_ERR_INVALID_ARG, "stencil capacity too large for shared memory");
+    }
+
+    int rc = set_device(h);
+    if (rc) {
+        delete h;
+        return rc;
+    }
+    if (cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        delete h;
+        return fail(MC_ERR_CUDA, "stream create");
+    }
+    h->stream = h->own_stream;
+
+    DevState &d = h->ds;
+    d.n_rep = n_rep;
+    d.n_sites = h->n_sites;
+    d.n_cells = h->n_cells;
+    d.n_act = h->n_act;
+    d.stencil_cap = cap;
+    d.precision = h->precision;
+    const int M_tot = h->n_sites / 3;
+    int4 *r0, *r1;
+    int *cc, *cs, *co, *so, *img, *err;
+    double *cde, *erun;
+    unsigned long long *stats;
+    if ((rc = h->alloc(&h->d_rep, n_rep)) || (rc = h->alloc(&h->d_par, n_rep)) || (rc = h->alloc(&h->d_ctr, n_rep)) ||
+        (rc = h->alloc(&h->d_model, 1)) || (rc = h->alloc(&h->d_mix, 1)) ||
+        (rc = h->alloc(&h->d_rep_of_site, h->n_sites)) || (rc = h->alloc(&h->d_act_off, n_rep + 1)) ||
+        (rc = h->alloc(&r0, h->n_sites)) || (rc = h->alloc(&r1, h->n_sites)) || (rc = h->alloc(&cc, h->n_cells)) ||
+        (rc = h->alloc(&cs, h->n_cells + 1)) || (rc = h->alloc(&co, h->n_sites)) || (rc = h->alloc(&so, h->n_sites)) ||
+        (rc = h->alloc(&img, 3 * (size_t)h->n_sites)) || (rc = h->alloc(&cde, h->n_cells)) ||
+        (rc = h->alloc(&stats, (size_t)STAT_N * n_rep)) || (rc = h->alloc(&erun, n_rep)) ||
+        (rc = h->alloc(&err, 1)) || (rc = h->alloc(&h->d_e_site, h->n_sites)) ||
+        (rc = h->alloc(&h->d_e_out, n_rep)) || (rc = h->alloc(&h->d_X, 3 * (size_t)h->n_sites)) ||
+        (rc = h->alloc(&h->d_types, h->n_sites)) || (rc = h->alloc(&h->obs.X0, 3 * (size_t)h->n_sites)) ||
+        (rc = h->alloc(&h->obs.kref, M_tot)) || (rc = h->alloc(&h->obs.u0, 3 * (size_t)M_tot)) ||
+        (rc = h->alloc(&h->d_fs, h->n_sites)) || (rc = h->alloc(&h->d_fscm, M_tot)) ||
+        (rc = h->alloc(&h->d_c2, M_tot)) || (rc = h->alloc(&h->d_q, 6 * 256)) ||
+        (rc = h->alloc(&h->d_obs_out, 3 * (size_t)n_rep))) {
+        mc_destroy(h);
+        return rc;
+    }
+    d.rep = h->d_rep;
+    d.par = h->d_par;
+    d.ctr = h->d_ctr;
+    d.model = h->d_model;
+    d.mix = h->d_mix;
+    d.rep_of_site = h->d_rep_of_site;
+    d.act_off = h->d_act_off;
+    d.rec[0] = r0;
+    d.rec[1] = r1;
+    d.cell_count = cc;
+    d.cell_start = cs;
+    d.cell_of = co;
+    d.slot_of = so;
+    d.img = img;
+    d.cell_dE = cde;
+    d.stats = stats;
+    d.e_run = erun;
+    d.err = err;
+
+    h->par_host.assign(n_rep, RepParam{1.0, 0, 0, 0});
+    auto up = [&](void *dst, const void *src, size_t bytes) {
+        return cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice) == cudaSuccess;
+    };
+    if (!up(h->d_rep, h->reps.data(), sizeof(RepInfo) * n_rep) || !up(h->d_model, &h->model_host, sizeof(ModelDev)) ||
+        !up(h->d_rep_of_site, rep_of_site.data(), sizeof(int) * h->n_sites) ||
+        !up(h->d_act_off, act_off.data(), sizeof(int) * (n_rep + 1)) ||
+        !up(h->d_par, h->par_host.data(), sizeof(RepParam) * n_rep)) {
+        mc_destroy(h);
+        return fail(MC_ERR_CUDA, "upload of tables failed");
+    }
+    if (phase_set_smem_limit(cap, h->wpb) != 0) {
+        mc_destroy(h);
+        return fail(MC_ERR_CUDA, "cannot reserve shared memory for the sweep kernel");
+    }
+    std::vector<int4> rec;
+    rc = pack_records(h, xyz, nullptr, types, rec);
+    if (rc == MC_OK) rc = rebuild_and_reset(h, rec);
+    if (rc) {
+        std::string msg = g_err;
+        mc_destroy(h);
+        return fail(rc, msg);
+    }
+    *out = h;
+    return MC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mc_create(mc_handle **out, double L, int n_mol, const double *xyz, const int32_t *types, const mc_params *params,
+              const mc_options *opts)
+{
+    const int32_t nm = n_mol;
+    return create_impl(out, 1, &L, &nm, xyz, types, params, opts);
+}
+
+int mc_create_batch(mc_handle **out, int n_rep, const double *L, const int32_t *n_mol, const double *xyz,
+                    const int32_t *types, const mc_params *params, const mc_options *opts)
+{
+    return create_impl(out, n_rep, L, n_mol, xyz, types, params, opts);
+}
+
+void mc_destroy(mc_handle *h)
+{
+    if (!h) return;
+    cudaSetDevice(h->device);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    for (int b = 0; b < 2; ++b)
+        if (h->graph[b]) cudaGraphExecDestroy(h->graph[b]);
+    for (auto &a : h->allocs) cudaFree(a.p);
+    if (h->own_stream) cudaStreamDestroy(h->own_stream);
+    delete h;
+}
+
+int mc_set_stream(mc_handle *h, void *stream)
+{
+    if (!h) return fail(MC_ERR_INVALID_ARG, "NULL handle");
+    h->stream = stream ? (cudaStream_t)stream : h->own_stream;
+    return MC_OK;
+}
+
+static int sweep_impl(mc_handle *h, int n_sweeps, const double *T, const mc_move_mix *mix, const uint64_t *seeds,
+                      bool same)
+{
+    if (!h) return fail(MC_ERR_INVALID_ARG, "NULL handle");
+    if (n_sweeps < 0) return fail(MC_ERR_INVALID_ARG, "n_sweeps < 0");
+    if (!T || !seeds) return fail(MC_ERR_INVALID_ARG, "NULL T or seeds");
+    int rc = check_mix(mix);
+    if (rc) return rc;
+    if ((rc = set_device(h))) return rc;
+    if ((rc = upload_params(h, T, mix, seeds, same))) return rc;
+    for (int s = 0; s < n_sweeps; ++s) {
+        if ((rc = ensure_graph(h, h->cur))) return rc;
+        CUDA_TRY(cudaGraphLaunch(h->graph[h->cur], h->stream));
+        h->cur ^= 1;
+    }
+    CUDA_TRY(cudaGetLastError());
+    return MC_OK;
+}
+
+int mc_sweep(mc_handle *h, int n_sweeps, double T, const mc_move_mix *mix, uint64_t seed)
+{
+    return sweep_impl(h, n_sweeps, &T, mix, &seed, true);
+}
+
+int mc_sweep_batch(mc_handle *h, int n_sweeps, const double *T, const mc_move_mix *mix, const uint64_t *seeds)
+{
+    return sweep_impl(h, n_sweeps, T, mix, seeds, false);
+}
+
+int mc_sweep_logged(mc_handle *h, int n_sweeps, const double *T, const mc_move_mix *mix, const uint64_t *seeds,
+                    mc_log_entry *log_out)
+{
+    if (!h || !log_out) return fail(MC_ERR_INVALID_ARG, "NULL handle or log");
+    if (n_sweeps < 0 || !T || !seeds) return fail(MC_ERR_INVALID_ARG, "bad arguments");
+    int rc = check_mix(mix);
+    if (rc) return rc;
+    if ((rc = set_device(h))) return rc;
+    if ((rc = upload_params(h, T, mix, seeds, false))) return rc;
+    if (n_sweeps == 0) return MC_OK;
+    uint64_t sweep0 = 0;
+    CUDA_TRY(cudaMemcpy(&sweep0, &h->d_ctr[0].sweep, sizeof(uint64_t), cudaMemcpyDeviceToHost));
+    const size_t n = (size_t)n_sweeps * (size_t)h->n_sites;
+    mc_log_entry *dlog = nullptr;
+    CUDA_TRY(cudaMalloc(&dlog, sizeof(mc_log_entry) * n));
+    cudaMemsetAsync(dlog, 0xff, sizeof(mc_log_entry) * n, h->stream);
+    LogArgs lg{dlog, n_sweeps, sweep0};
+    for (int s = 0; s < n_sweeps; ++s) {
+        launch_cell_list(h->ds, h->cur, h->cur ^ 1, h->stream);
+        launch_phases(h->ds, h->cur ^ 1, h->wpb, lg, h->stream);
+        h->cur ^= 1;
+    }
+    cudaError_t e = cudaMemcpyAsync(log_out, dlog, sizeof(mc_log_entry) * n, cudaMemcpyDeviceToHost, h->stream);
+    cudaError_t e2 = cudaStreamSynchronize(h->stream);
+    cudaFree(dlog);
+    if (e != cudaSuccess || e2 != cudaSuccess)
+        return fail(MC_ERR_CUDA, std::string("logged sweep: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+    return check_device_errors(h);
+}
+
+int mc_sweep_timed(mc_handle *h, int n_sweeps, const double *T, const mc_move_mix *mix, const uint64_t *seeds,
+                   double *ms_out)
+{
+    if (!h || !ms_out || !T || !seeds || n_sweeps < 0) return fail(MC_ERR_INVALID_ARG, "bad arguments");
+    int rc = check_mix(mix);
+    if (rc) return rc;
+    if ((rc = set_device(h))) return rc;
+    if ((rc = upload_params(h, T, mix, seeds, false))) return rc;
+    cudaEvent_t ev[4];
+    for (auto &e : ev) CUDA_TRY(cudaEventCreate(&e));
+    double tot[3] = {0.0, 0.0, 0.0};
+    LogArgs none{nullptr, 0, 0};
+    for (int s = 0; s < n_sweeps; ++s) {
+        cudaEventRecord(ev[0], h->stream);
+        launch_cell_list(h->ds, h->cur, h->cur ^ 1, h->stream);
+        cudaEventRecord(ev[1], h->stream);
+        launch_colour_phases(h->ds, h->cur ^ 1, h->wpb, none, h->stream);
+        cudaEventRecord(ev[2], h->stream);
+        launch_finalize(h->ds, h->stream);
+        cudaEventRecord(ev[3], h->stream);
+        h->cur ^= 1;
+        cudaError_t e = cudaEventSynchronize(ev[3]);
+        if (e != cudaSuccess) {
+            for (auto &x : ev) cudaEventDestroy(x);
+            return fail(MC_ERR_CUDA, std::string("timed sweep: ") + cudaGetErrorString(e));
+        }
+        for (int k = 0; k < 3; ++k) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
+            tot[k] += ms;
+        }
+    }
+    for (auto &x : ev) cudaEventDestroy(x);
+    for (int k = 0; k < 3; ++k) ms_out[k] = tot[k];
+    return check_device_errors(h);
+}
+
+int mc_energy_device(mc_handle *h, double *dev_E_out)
+{
+    if (!h || !dev_E_out) return fail(MC_ERR_INVALID_ARG, "NULL argument");
+    int rc = set_device(h);
+    if (rc) return rc;
+    if ((rc = enqueue_energy(h))) return rc;
+    CUDA_TRY(cudaMemcpyAsync(dev_E_out, h->d_e_out, sizeof(double) * h->n_rep, cudaMemcpyDeviceToDevice, h->stream));
+    return MC_OK;
+}
+
+int mc_sync(mc_handle *h)
+{
+    if (!h) return fail(MC_ERR_INVALID_ARG, "NULL handle");
+    int rc = set_device(h);
+    if (rc) return rc;
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    CUDA_TRY(cudaGetLastError());
+    return check_device_errors(h);
+}
+
+int mc_energy(mc_handle *h, double *E_out)
+{
+    if (!h || !E_out) return fail(MC_ERR_INVALID_ARG, "NULL argument");
+    int rc = set_device(h);
+    if (rc) return rc;
+    if ((rc = enqueue_energy(h))) return rc;
+    CUDA_TRY(cudaMemcpyAsync(E_out, h->d_e_out, sizeof(double) * h->n_rep, cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return check_device_errors(h);
+}
+
+static int fetch_records(mc_handle *h, std::vector<int4> &rec, std::vector<int> &img)
+{
+    rec.resize(h->n_sites);
+    img.resize(3 * (size_t)h->n_sites);
+    CUDA_TRY(cudaMemcpyAsync(rec.data(), h->ds.rec[h->cur], sizeof(int4) * h->n_sites, cudaMemcpyDeviceToHost,
+                             h->stream));
+    CUDA_TRY(cudaMemcpyAsync(img.data(), h->ds.img, sizeof(int) * 3 * (size_t)h->n_sites, cudaMemcpyDeviceToHost,
+                             h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return check_device_errors(h);
+}
+
+static int site_of(const mc_handle *h, int r, const int4 &v)
+{
+    return h->reps[r].site_off + 3 * (int)((uint32_t)v.w >> 4) + ((v.w >> 2) & 3);
+}
+
+int mc_state(mc_handle *h, double *xyz_out, int32_t *types_out, mc_stats *stats_out)
+{
+    if (!h) return fail(MC_ERR_INVALID_ARG, "NULL handle");
+    int rc = set_device(h);
+    if (rc) return rc;
+    if (xyz_out || types_out) {
+        std::vector<int4> rec;
+        std::vector<int> img;
+        if ((rc = fetch_records(h, rec, img))) return rc;
+        for (int r = 0; r < h->n_rep; ++r) {
+            const RepInfo &ri = h->reps[r];
+            for (int i = 0; i < ri.n_sites; ++i) {
+                const int4 v = rec[ri.site_off + i];
+                const int s = site_of(h, r, v);
+                if (xyz_out) {
+                    xyz_out[3 * (size_t)s + 0] = (double)(uint32_t)v.x * ri.h;
+                    xyz_out[3 * (size_t)s + 1] = (double)(uint32_t)v.y * ri.h;
+                    xyz_out[3 * (size_t)s + 2] = (double)(uint32_t)v.z * ri.h;
+                }
+                if (types_out) types_out[s] = v.w & 3;
+            }
+        }
+    }
+    if (stats_out) {
+        std::vector<unsigned long long> st((size_t)STAT_N * h->n_rep);
+        std::vector<double> e(h->n_rep);
+        CUDA_TRY(cudaMemcpyAsync(st.data(), h->ds.stats, sizeof(unsigned long long) * st.size(), cudaMemcpyDeviceToHost,
+                                 h->stream));
+        CUDA_TRY(cudaMemcpyAsync(e.data(), h->ds.e_run, sizeof(double) * h->n_rep, cudaMemcpyDeviceToHost, h->stream));
+        CUDA_TRY(cudaStreamSynchronize(h->stream));
+        for (int r = 0; r < h->n_rep; ++r) {
+            mc_stats &s = stats_out[r];
+            const unsigned long long *v = st.data() + (size_t)STAT_N * r;
+            for (int k = 0; k < 4; ++k) {
+                s.attempts[k] = v[STAT_ATT + k];
+                s.accepts[k] = v[STAT_ACC + k];
+            }
+            s.rejected_geometry = v[STAT_REJ_GEOM];
+            s.rejected_bond = v[STAT_REJ_BOND];
+            s.pair_evals = v[STAT_PAIRS];
+            s.fp64_rechecks = v[STAT_RECHECK];
+            s.sweeps = v[STAT_SWEEPS];
+            s.e_run = e[r];
+        }
+        return check_device_errors(h);
+    }
+    return MC_OK;
+}
+
+int mc_state_fixed(mc_handle *h, uint32_t *q_out, int64_t *X_out, int32_t *types_out)
+{
+    if (!h) return fail(MC_ERR_INVALID_ARG, "NULL handle");
+    int rc = set_device(h);
+    if (rc) return rc;
+    std::vector<int4> rec;
+    std::vector<int> img;
+    if ((rc = fetch_records(h, rec, img))) return rc;
+    for (int r = 0; r < h->n_rep; ++r) {
+        const RepInfo &ri = h->reps[r];
+        for (int i = 0; i < ri.n_sites; ++i) {
+            const int4 v = rec[ri.site_off + i];
+            const int s = site_of(h, r, v);
+            const uint32_t q3[3] = {(uint32_t)v.x, (uint32_t)v.y, (uint32_t)v.z};
+            for (int ax = 0; ax < 3; ++ax) {
+                if (q_out) q_out[3 * (size_t)s + ax] = q3[ax];
+                if (X_out) X_out[3 * (size_t)s + ax] = (int64_t)q3[ax] + ((int64_t)img[3 * (size_t)s + ax] << 32);
+            }
+            if (types_out) types_out[s] = v.w & 3;
+        }
+    }
+    return MC_OK;
+}
+
+int mc_set_state(mc_handle *h, const double *xyz, const int32_t *types)
+{
+    if (!h || !xyz || !types) return fail(MC_ERR_INVALID_ARG, "NULL argument");
+    int rc = set_device(h);
+    if (rc) return rc;
+    std::vector<int4> rec;
+    if ((rc = pack_records(h, xyz, nullptr, types, rec))) return rc;
+    return rebuild_and_reset(h, rec);
+}
+
+int mc_set_state_fixed(mc_handle *h, const uint32_t *q, const int64_t *X, const int32_t *types)
+{
+    if (!h || !q || !types) return fail(MC_ERR_INVALID_ARG, "NULL argument");
+    int rc = set_device(h);
+    if (rc) return rc;
+    std::vector<int4> rec;
+    if ((rc = pack_records(h, nullptr, q, types, rec))) return rc;
+    if (!X) return rebuild_and_reset(h, rec);
+    std::vector<int> img(3 * (size_t)h->n_sites);
+    for (size_t k = 0; k < img.size(); ++k) {
+        const int64_t d = X[k] - (int64_t)q[k];
+        if (d % 4294967296LL != 0) return fail(MC_ERR_INVALID_ARG, "X - q is not a multiple of 2^32");
+        img[k] = (int)(d / 4294967296LL);
+    }
+    return rebuild_and_reset(h, rec, &img);
+}
+
+int mc_set_sweep(mc_handle *h, uint64_t sweep)
+{
+    if (!h) return fail(MC_ERR_INVALID_ARG, "NULL handle");
+    int rc = set_device(h);
+    if (rc) return rc;
+    std::vector<RepCtr> c(h->n_rep);
+    CUDA_TRY(cudaMemcpyAsync(c.data(), h->d_ctr, sizeof(RepCtr) * h->n_rep, cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    for (auto &x : c) x.sweep = sweep;
+    CUDA_TRY(cudaMemcpyAsync(h->d_ctr, c.data(), sizeof(RepCtr) * h->n_rep, cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return MC_OK;
+}
+
+int mc_reset_stats(mc_handle *h)
+{
+    if (!h) return fail(MC_ERR_INVALID_ARG, "NULL handle");
+    int rc = set_device(h);
+    if (rc) return rc;
+    CUDA_TRY(cudaMemsetAsync(h->ds.stats, 0, sizeof(unsigned long long) * STAT_N * h->n_rep, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return MC_OK;
+}
+
+int mc_set_t0(mc_handle *h)
+{
+    if (!h) return fail(MC_ERR_INVALID_ARG, "NULL handle");
+    int rc = set_device(h);
+    if (rc) return rc;
+    launch_gather(h->ds, h->cur, h->d_X, h->d_types, h->stream);
+    launch_set_t0(h->ds, h->d_X, h->d_types, h->obs, h->stream);
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    h->has_t0 = true;
+    return MC_OK;
+}
+
+int mc_observables(mc_handle *h, const double *qvec_atom, int n_qa, const double *qvec_cm, int n_qc, double *out,
+                   double *fs_atom, double *fscm_mol, double *c2_mol)
+{
+    if (!h || !qvec_atom || !qvec_cm || !out) return fail(MC_ERR_INVALID_ARG, "NULL argument");
+    if (!h->has_t0) return fail(MC_ERR_INVALID_ARG, "mc_set_t0 has not been called");
+    if (n_qa < 1 || n_qa > 256 || n_qc < 1 || n_qc > 256) return fail(MC_ERR_INVALID_ARG, "1 <= n_q <= 256");
+    int rc = set_device(h);
+    if (rc) return rc;
+    CUDA_TRY(cudaMemcpyAsync(h->d_q, qvec_atom, sizeof(double) * 3 * n_qa, cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(cudaMemcpyAsync(h->d_q + 3 * 256, qvec_cm, sizeof(double) * 3 * n_qc, cudaMemcpyHostToDevice, h->stream));
+    launch_gather(h->ds, h->cur, h->d_X, h->d_types, h->stream);
+    launch_observables(h->ds, h->d_X, h->obs, h->d_q, n_qa, h->d_q + 3 * 256, n_qc, h->d_fs, h->d_fscm, h->d_c2,
+                       h->d_obs_out, h->stream);
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaMemcpyAsync(out, h->d_obs_out, sizeof(double) * 3 * h->n_rep, cudaMemcpyDeviceToHost, h->stream));
+    const size_t M = (size_t)h->n_sites / 3;
+    if (fs_atom)
+        CUDA_TRY(cudaMemcpyAsync(fs_atom, h->d_fs, sizeof(double) * h->n_sites, cudaMemcpyDeviceToHost, h->stream));
+    if (fscm_mol) CUDA_TRY(cudaMemcpyAsync(fscm_mol, h->d_fscm, sizeof(double) * M, cudaMemcpyDeviceToHost, h->stream));
+    if (c2_mol) CUDA_TRY(cudaMemcpyAsync(c2_mol, h->d_c2, sizeof(double) * M, cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return MC_OK;
+}
+
+int mc_get_info(mc_handle *h, mc_info *info)
+{
+    if (!h || !info) return fail(MC_ERR_INVALID_ARG, "NULL argument");
+    info->n_rep = h->n_rep;
+    info->precision = h->precision;
+    info->stencil_cap = h->stencil_cap;
+    info->total_sites = h->n_sites;
+    info->total_cells = h->n_cells;
+    int mx = 0;
+    for (auto &r : h->reps) mx = std::max(mx, r.nc);
+    info->max_cells_per_axis = mx;
+    info->recheck_gap = h->recheck_gap;
+    return MC_OK;
+}
+
+const char *mc_last_error(void)
+{
+    return g_err.c_str();
+}
+
+}  // extern "C"

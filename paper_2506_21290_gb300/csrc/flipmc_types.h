@@ -1,0 +1,101 @@
+// Structures shared by the host engine and the device kernels.
+#pragma once
+
+#include <cstdint>
+
+#include "../../include/flipmc.h"
+
+namespace flipmc {
+
+// Potential tables, type pair ab = 3a + b (Eq. 1-2).
+struct ModelDev {
+    double s2[9];    // sigma_ab^2
+    double rc2[9];   // (2^(1/3)) sigma_ab^2: WCA cutoff squared
+    double R2[9];    // (R0 sigma_ab)^2: FENE divergence squared
+    double eps, e4, nke, ke;
+    float s2f[9], rc2f[9], R2f[9], invR2f[9];
+    float epsf, e4f, nkef, kef;
+    float bond_guard_f;   // FP32 bond-length ratio beyond which FP32 defers to FP64
+    float recheck_gap_f;
+};
+
+// Move-mix parameters of the current sweep call.
+struct MixDev {
+    uint64_t thr[3];      // move-type thresholds on a 32-bit word
+    double rot_a;
+};
+
+// Per-replica static layout.
+struct RepInfo {
+    int n_sites;
+    int site_off;    // first global site
+    int nc;          // cells per axis
+    int cell_off;    // first global cell
+    int act_off;     // first global active-cell slot within a colour
+    int pad;
+    double L, h, inv_h;
+    float hf;
+    float pad2;
+};
+
+// Per-replica parameters of the current sweep call (written by the host).
+struct RepParam {
+    double T;
+    uint64_t seed;
+    int32_t D_atom;      // atom step half-width in fixed-point units
+    int32_t D_mol;       // molecule step half-width in fixed-point units
+};
+
+// Per-replica counters owned by the device.
+struct RepCtr {
+    uint64_t sweep;      // number of the sweep being (or next to be) run
+    uint32_t shift[4];   // grid shift of that sweep (x, y, z)
+};
+
+// counters per replica (uint64)
+enum {
+    STAT_ATT = 0,       // [4]
+    STAT_ACC = 4,       // [4]
+    STAT_REJ_GEOM = 8,
+    STAT_REJ_BOND = 9,
+    STAT_PAIRS = 10,
+    STAT_RECHECK = 11,
+    STAT_SWEEPS = 12,
+    STAT_N = 16
+};
+
+// error bits
+enum {
+    ERR_STENCIL = 1,    // neighbourhood larger than the staging capacity
+    ERR_TERMS = 2,      // FP64 ordered-sum buffer overflow
+    ERR_TIMEOUT = 4,
+};
+
+// Everything a kernel needs, by value.
+struct DevState {
+    int n_rep;
+    int n_sites;         // total over replicas
+    int n_cells;         // total over replicas
+    int n_act;           // active cells per colour, total over replicas
+    int stencil_cap;
+    int precision;
+    const RepInfo *rep;
+    const RepParam *par;
+    RepCtr *ctr;
+    const ModelDev *model;
+    const MixDev *mix;
+    const int *rep_of_site;
+    const int *act_off;  // n_rep + 1 prefix of (nc/2)^3
+    int4 *rec[2];        // double-buffered records {qx, qy, qz, w}, cell-sorted
+    int *cell_count;
+    int *cell_start;     // n_cells + 1
+    int *cell_of;
+    int *slot_of;
+    int *img;            // 3 per site, indexed by global site index
+    double *cell_dE;     // accepted Delta E per cell in the last sweep
+    unsigned long long *stats;   // STAT_N per replica
+    double *e_run;       // per replica
+    int *err;
+};
+
+}  // namespace flipmc
