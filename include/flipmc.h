@@ -278,6 +278,32 @@ int mc_observables(mc_handle *h, const double *qvec_atom, int n_qa, const double
 /* Static facts of the handle. */
 int mc_get_info(mc_handle *h, mc_info *info);
 
+/*
+ * Total FP64 energy (Eq. 1 + Eq. 2, every pair once) of one configuration
+ * that already sits in the caller's device memory, for callers that cannot
+ * allocate device memory: code running inside another framework's memory
+ * pool or under a fixed device-memory budget, or code that may only enqueue
+ * kernels on a stream it was given.  The paper has no counterpart; this is an
+ * interface convenience.
+ *   L: box side; n_mol: molecules, 1 <= n_mol <= 21845 (at most 65536 atoms);
+ *   dev_q: 3*3*n_mol fixed-point positions (q = floor(frac(x/L) 2^32)),
+ *   dev_types: 3*n_mol types in {0,1,2}, dev_E_out: one double, all three
+ *   device memory of the current device, owned by the caller;
+ *   params: host, NULL picks the paper's potential; stream: cudaStream_t
+ *   (NULL: the legacy default stream).
+ * Allocates nothing: the working space is a fixed __device__ array of this
+ * library (about 3.5 MB on every GPU that loads it, kept until exit).  All
+ * calls on a device share that array: calls whose work overlaps on the GPU
+ * race and must be serialised by the caller.  The first call on a device
+ * looks up the array's address and should come before any stream capture.
+ * Enqueues only; the result is ready when the stream reaches it.  A type
+ * outside {0,1,2} or a broken bond gives NaN (or +inf).
+ * Errors: INVALID_ARG (sizes beyond the maximum, NULL pointers, box smaller
+ * than two interaction ranges), NO_DEVICE, CUDA.
+ */
+int mc_energy_noalloc(double L, int n_mol, const uint32_t *dev_q, const int32_t *dev_types, const mc_params *params,
+                      double *dev_E_out, void *stream);
+
 /* Message describing the calling thread's last error ("" if none). */
 const char *mc_last_error(void);
 

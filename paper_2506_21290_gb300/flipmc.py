@@ -104,6 +104,7 @@ def load():
         "mc_observables": ([vp, vp, i32, vp, i32, vp, vp, vp, vp], i32),
         "mc_get_info": ([vp, vp], i32),
         "mc_last_error": ([], C.c_char_p),
+        "mc_energy_noalloc": ([dbl, i32, vp, vp, vp, vp, vp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -284,6 +285,15 @@ def mc_get_info(h):
 
 def mc_last_error():
     return load().mc_last_error().decode()
+
+
+def mc_energy_noalloc(L, n_mol, dev_q_ptr, dev_types_ptr, pot, dev_out_ptr, stream_ptr=0):
+    """Energy of a configuration in caller device memory, with no device
+    allocation by the library (for callers that cannot allocate); raw device
+    pointers in, one double written at dev_out_ptr.  Returns the C code."""
+    p = make_params(pot)
+    return load().mc_energy_noalloc(float(L), int(n_mol), C.c_void_p(dev_q_ptr), C.c_void_p(dev_types_ptr),
+                                    C.byref(p), C.c_void_p(dev_out_ptr), C.c_void_p(stream_ptr))
 
 
 def stats_dict(s):
