@@ -49,6 +49,10 @@ def parse():
     ap.add_argument("--workload", default="single-1000", choices=sorted(W.WORKLOADS))
     ap.add_argument("--sweeps-per-step", type=int, default=0, help="0: workload default")
     ap.add_argument("--precision", default="", choices=["", "fp32", "fp64"])
+    ap.add_argument("--launch-mode", type=int, default=0, choices=[0, 1, 2],
+                    help="0 auto, 1 a CUDA graph per sweep, 2 one persistent launch per step")
+    ap.add_argument("--warps-per-cell", type=int, default=0, choices=[0, 1, 2, 4])
+    ap.add_argument("--recheck-gap", type=float, default=0.0, help="FP32 decision margin (0: library default)")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -206,9 +210,12 @@ def run_native(args):
     precision = args.precision or wl["precision"]
     sps = args.sweeps_per_step or DEFAULT_SPS[args.workload]
     mix = W.PAPER_MIX
-    h = F.Handle(wl["L"], wl["xyz"], wl["types"], W.PAPER_POT, precision=precision, device=local, n_mol=wl["n_mol"])
+    h = F.Handle(wl["L"], wl["xyz"], wl["types"], W.PAPER_POT, precision=precision, device=local, n_mol=wl["n_mol"],
+                 launch_mode=args.launch_mode, warps_per_cell=args.warps_per_cell, recheck_gap=args.recheck_gap)
     N = h.N
-    stream = torch.cuda.current_stream()
+    # a dedicated stream: the library enqueues on it, the events are recorded on it
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     h.set_stream(stream.cuda_stream)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     e_dev = torch.zeros(h.n_rep, dtype=torch.float64, device="cuda")
@@ -231,15 +238,19 @@ def run_native(args):
     for _ in range(args.steps):
         flush.fill_(1)                 # evict the state from L2 between timed steps
         a = torch.cuda.Event(enable_timing=True)
+        m = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        step()
+        h.sweep(sps, wl["T"], mix, wl["seeds"])   # the sweep launch(es) of the step
+        m.record(stream)
+        h.energy_device(e_dev.data_ptr())         # FP64 energy recompute
         b.record(stream)
-        evs.append((a, b))
+        evs.append((a, m, b))
     torch.cuda.synchronize()
     h.sync()
     clk = clocks.stop()
-    ms = sum(a.elapsed_time(b) for a, b in evs)
+    ms = sum(a.elapsed_time(b) for a, m, b in evs)
+    sweep_ms = sum(a.elapsed_time(m) for a, m, b in evs)
     st1 = h.stats()
     attempts = sum(sum(s1["attempts"]) - sum(s0["attempts"]) for s0, s1 in zip(st0, st1))
     pairs = sum(s1["pair_evals"] - s0["pair_evals"] for s0, s1 in zip(st0, st1))
@@ -259,15 +270,16 @@ def run_native(args):
     value = attempts_all / (ms_max / 1000.0)
     pair_rate = pairs_all / (ms_max / 1000.0)
 
-    # per-kernel durations for the roofline: CUDA events around each stage
+    # the dominant kernel is the sweep kernel: one persistent launch per step
+    # (events around it in every timed step, on its stream); per-stage times of
+    # the separate-kernel path are reported next to it
+    info = h.info
+    persistent = info.get("launch_mode", 0) != 1
+    launch_ms = sweep_ms / args.steps
+    flops_per_launch = FLOPS_PER_PAIR_EVAL * pairs / args.steps
+    achieved = flops_per_launch / (launch_ms / 1000.0) / 1e12
     n_prof = max(2, min(20, sps))
-    st2 = h.stats()
     stage_ms = h.sweep_timed(n_prof, wl["T"], mix, wl["seeds"])
-    st3 = h.stats()
-    prof_pairs = sum(s3["pair_evals"] - s2["pair_evals"] for s2, s3 in zip(st2, st3))
-    phase_launch_ms = stage_ms[1] / (8 * n_prof)
-    flops_per_launch = FLOPS_PER_PAIR_EVAL * prof_pairs / (8 * n_prof)
-    achieved = flops_per_launch / (phase_launch_ms / 1000.0) / 1e12
     peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
     peak_at_clock = (SM_COUNT * FP32_LANES_PER_SM * 2 * clk["sm_mhz"] * 1e6 / 1e12) if clk.get("sm_mhz") else None
 
@@ -315,15 +327,20 @@ def run_native(args):
         "fp64_recheck_rate": rechecks / max(attempts, 1),
         "acceptance": [accepts[k] / att_k[k] if att_k[k] else None for k in range(4)],
         "geometry_reject_rate": geom / max(attempts, 1),
-        "roofline": {"bound": "alu", "kernel": "phase_kernel<FP32>" if precision == "fp32" else "phase_kernel<FP64>",
+        "roofline": {"bound": "alu",
+                     "kernel": ("sweep_persistent" if persistent else "phase_kernel")
+                               + ("<FP32,W=%d>" if precision == "fp32" else "<FP64,W=%d>") % info["warps_per_cell"],
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                      "traffic": None, "peak_basis": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (max clock)",
                      "peak_at_measured_clock": peak_at_clock,
-                     "launch_ms": phase_launch_ms, "flops_per_launch": flops_per_launch,
-                     "stage_ms_per_sweep": [x / n_prof for x in stage_ms]},
+                     "launch_ms": launch_ms, "flops_per_launch": flops_per_launch,
+                     "flops_per_pair_eval": FLOPS_PER_PAIR_EVAL,
+                     "separate_kernel_stage_ms_per_sweep": {"cell_list": stage_ms[0] / n_prof,
+                                                            "8_phases": stage_ms[1] / n_prof,
+                                                            "finalize": stage_ms[2] / n_prof}},
         "cpu_baseline": cpu,
         "e2e": e2e,
-        "gpu_launches": args.steps * (sps * launches_per_sweep + 2),
+        "gpu_launches": args.steps * ((1 + 1) if persistent else sps * launches_per_sweep) + args.steps * 2,
         "clocks": clk,
     }
     print(json.dumps(line), flush=True)

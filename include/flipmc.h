@@ -101,13 +101,21 @@ typedef struct {
  * per axis (even, >= 2), 0 picks the largest even n_c whose cell side is at
  * least R0 * max bonded sigma_ab (the longest possible interaction).
  * recheck_gap: FP32 decision margin (0 picks 1e-4).  device: CUDA device
- * ordinal.  stencil_cap: atoms staged per cell neighbourhood (0 = automatic). */
+ * ordinal.  stencil_cap: atoms staged per cell neighbourhood (0 = automatic).
+ * warps_per_cell: 1, 2 or 4 warps per cell, each evaluating one of the cell's
+ * consecutive attempts, committed in order (0 = chosen from the number of
+ * cells); results do not depend on it.  launch_mode: 0 = one persistent
+ * cooperative launch per mc_sweep call when the device supports it, else a
+ * CUDA graph per sweep; 1 = graphs; 2 = persistent (INVALID_ARG if
+ * unsupported). */
 typedef struct {
     int precision;
     int n_cells;
     int device;
     int stencil_cap;
     double recheck_gap;
+    int warps_per_cell;
+    int launch_mode;
 } mc_options;
 
 /* Per-replica counters since creation (or mc_reset_stats). */
@@ -131,6 +139,10 @@ typedef struct {
     int total_cells;
     int max_cells_per_axis;
     double recheck_gap;
+    int warps_per_cell;
+    int active_cells_per_colour;
+    int launch_mode;          /* 1: a CUDA graph per sweep; 2: one persistent launch per call */
+    int persistent_blocks;    /* blocks of the persistent launch (0 with graphs) */
 } mc_info;
 
 /* One attempted move as recorded by mc_sweep_logged(). */

@@ -27,7 +27,15 @@ void launch_phases(const DevState &d, int buf, int warps_per_block, const LogArg
 // the same two stages, separately (for per-stage timing)
 void launch_colour_phases(const DevState &d, int buf, int warps_per_block, const LogArgs &lg, cudaStream_t st);
 void launch_finalize(const DevState &d, cudaStream_t st);
-size_t phase_smem_bytes(int stencil_cap, int warps_per_block);
-int phase_set_smem_limit(int stencil_cap, int warps_per_block);
+size_t phase_smem_bytes(int stencil_cap, int rec_cap, int warps_per_cell);
+int phase_set_smem_limit(int bytes_needed);
+
+// Persistent sweeps: co-resident blocks for one cooperative launch (0 when the
+// device cannot launch cooperatively), and the launch itself (n_sweeps whole
+// sweeps starting from records in buf; bar: 2 zeroed words; scan_tot: one int
+// per block).  Returns 0 or a cudaError_t.
+int persistent_grid(const DevState &d, int warps_per_cell, int max_blocks);
+int launch_persistent(const DevState &d, int buf, int n_sweeps, int warps_per_cell, int grid, unsigned int *bar,
+                      int *scan_tot, cudaStream_t st);
 
 }  // namespace flipmc

@@ -1,0 +1,104 @@
+// Per-item bodies of the cell-list build, shared by the stand-alone kernels
+// (cell_list.cu) and the persistent sweep kernel (sweep.cu).
+//
+// The grid of a replica is n_c^3 cells of side L/n_c, shifted by the sweep's
+// random 32-bit offset per axis; an atom's cell along an axis is
+// ((q + shift) * n_c) >> 32 on its 32-bit fixed-point coordinate q.
+#pragma once
+
+#include "flipmc_device.cuh"
+
+namespace flipmc {
+
+// Cell of atom g under the sweep's shift; slot by atomic count.  The
+// replica's first atom also publishes the shift.
+__device__ __forceinline__ void cl_count_item(const DevState &d, int buf, int g)
+{
+    const int r = d.rep_of_site[g];
+    const RepInfo ri = d.rep[r];
+    RepCtr *ct = d.ctr + r;
+    const U4 s = rng_block(0xFFFFFFFFu, 0xFFFFFFFFu, ct->sweep, d.par[r].seed);
+    if (g == ri.site_off) {
+        ct->shift[0] = s.x;
+        ct->shift[1] = s.y;
+        ct->shift[2] = s.z;
+    }
+    const uint32_t shift[3] = {s.x, s.y, s.z};
+    const int4 rc = d.rec[buf][g];
+    const int c = ri.cell_off + cell_local((uint32_t)rc.x, (uint32_t)rc.y, (uint32_t)rc.z, shift, ri.nc);
+    d.cell_of[g] = c;
+    d.slot_of[g] = atomicAdd(d.cell_count + c, 1);
+}
+
+__device__ __forceinline__ void cl_scatter_item(const DevState &d, int buf_in, int buf_out, int g)
+{
+    d.rec[buf_out][d.cell_start[d.cell_of[g]] + d.slot_of[g]] = d.rec[buf_in][g];
+}
+
+// The random words and Metropolis threshold of every attempt of the sweep.
+// Attempt a of cell c (a < occupancy) is slot start(c) + a; its words are the
+// Philox blocks (2a, c, sweep) and (2a+1, c, sweep) under the replica's seed;
+// its threshold is -T ln u with u = (2 u52 + 1) 2^-53 from the first block.
+__device__ __forceinline__ void attempt_randoms(const DevState &d, int r, int cellL, int slot, int a)
+{
+    const uint64_t sweep = d.ctr[r].sweep;
+    const uint64_t seed = d.par[r].seed;
+    const U4 b0 = rng_block((uint32_t)(2 * a), (uint32_t)cellL, sweep, seed);
+    const U4 b1 = rng_block((uint32_t)(2 * a + 1), (uint32_t)cellL, sweep, seed);
+    d.att_rnd[2 * (size_t)slot] = make_uint4(b0.x, b0.y, b0.z, b0.w);
+    d.att_rnd[2 * (size_t)slot + 1] = make_uint4(b1.x, b1.y, b1.z, b1.w);
+    const unsigned long long u52 = ((unsigned long long)b0.z << 20) | (unsigned long long)(b0.w >> 12);
+    const double T = d.par[r].T;
+    if (d.precision == MC_PREC_FP64) {
+        const double u = __dmul_rn((double)(2ull * u52 + 1ull), 0x1p-53);
+        d.att_thr64[slot] = -__dmul_rn(T, ln_series(u));
+    } else {
+        const float uf = __ull2float_rn(2ull * u52 + 1ull) * 0x1p-53f;
+        d.att_thr32[slot] = -(float)T * __logf(uf);
+    }
+}
+
+// Order the atoms of cell c by site index (the record word orders by
+// molecule, then slot), so the layout after a build does not depend on the
+// order in which the atomic counts were taken; then draw the random numbers of
+// the cell's attempts (when the sweep needs them).  One warp.
+__device__ __forceinline__ void cl_order_cell(const DevState &d, int buf, int c, int lane)
+{
+    const int start = d.cell_start[c];
+    const int n = d.cell_start[c + 1] - start;
+    int4 *seg = d.rec[buf] + start;
+    if (d.att_rnd != nullptr && n > 0) {
+        const int r = d.rep_of_site[start];
+        const int cellL = c - d.rep[r].cell_off;
+        for (int a = lane; a < n; a += 32) attempt_randoms(d, r, cellL, start + a, a);
+    }
+    if (n <= 1) return;
+    if (n <= 32) {
+        int4 mine = lane < n ? seg[lane] : make_int4(0, 0, 0, 0x7fffffff);
+        const unsigned key = (unsigned)mine.w;
+        int rank = 0;
+        for (int m = 0; m < n; ++m) {
+            const unsigned other = __shfl_sync(0xffffffffu, key, m);
+            rank += other < key;
+        }
+        __syncwarp();
+        if (lane < n) seg[rank] = mine;
+        __syncwarp();
+        return;
+    }
+    // larger cells (small boxes only): insertion sort by one lane
+    if (lane == 0) {
+        for (int i = 1; i < n; ++i) {
+            const int4 v = seg[i];
+            int j = i - 1;
+            while (j >= 0 && (unsigned)seg[j].w > (unsigned)v.w) {
+                seg[j + 1] = seg[j];
+                --j;
+            }
+            seg[j + 1] = v;
+        }
+    }
+    __syncwarp();
+}
+
+}  // namespace flipmc

@@ -43,6 +43,7 @@ int fail(int code, const std::string &msg)
 
 const double kCbrt2 = 0x1.428a2f98d728bp+0;   // double nearest 2^(1/3)
 const double kTwo32 = 4294967296.0;
+const int kMaxPersistentBlocks = 8192;
 
 // x -> floor(frac(x / L) * 2^32), the library's quantisation of positions
 uint32_t quantize(double x, double L)
@@ -69,6 +70,12 @@ struct mc_handle {
     int n_cells = 0;
     int n_act = 0;
     int stencil_cap = 0;
+    int full_rec = 1;
+    int own_cap = 0;
+    size_t smem_bytes = 0;
+    int pgrid = 0;                       // blocks of the persistent sweep (0: CUDA graphs instead)
+    unsigned int *d_bar = nullptr;       // grid barrier words
+    int *d_scan_tot = nullptr;           // per-block scan totals of the persistent sweep
     int wpb = 4;
     double recheck_gap = 1e-4;
     mc_params params{};
@@ -409,7 +416,8 @@ int create_impl(mc_handle **out, int n_rep, const double *L, const int32_t *n_mo
 
     // layout
     long long sites = 0, cells = 0, act = 0;
-    double max_stencil = 0.0;
+    double max_stencil = 0.0, max_own = 0.0;
+    bool any_small = false;
     std::vector<int> act_off(n_rep + 1, 0), rep_of_site;
     for (int r = 0; r < n_rep; ++r) {
         if (n_mol[r] < 1) {
@@ -449,9 +457,15 @@ int create_impl(mc_handle **out, int n_rep, const double *L, const int32_t *n_mo
         cells += (long long)nc * nc * nc;
         act += (long long)(nc / 2) * (nc / 2) * (nc / 2);
         act_off[r + 1] = (int)act;
+        // neighbourhood and own-cell sizes: mean plus six standard deviations
+        // (counts are at most Poisson-distributed in a liquid) and a margin
         const double per_cell = (double)ri.n_sites / ((double)nc * nc * nc);
-        const double st = (nc == 2) ? (double)ri.n_sites : 27.0 * per_cell * 1.6 + 64.0;
+        const double mean_nb = 27.0 * per_cell;
+        const double st = (nc == 2) ? (double)ri.n_sites : mean_nb + 6.0 * std::sqrt(mean_nb) + 32.0;
         max_stencil = std::max(max_stencil, std::min(st, (double)ri.n_sites));
+        const double own = (nc == 2) ? (double)ri.n_sites : per_cell + 6.0 * std::sqrt(per_cell) + 16.0;
+        max_own = std::max(max_own, std::min(own, (double)ri.n_sites));
+        any_small = any_small || nc == 2;
         if (sites > (1LL << 30)) {
             delete h;
             return fail(MC_ERR_INVALID_ARG, "too many sites");
@@ -460,12 +474,23 @@ int create_impl(mc_handle **out, int n_rep, const double *L, const int32_t *n_mo
     h->n_sites = (int)sites;
     h->n_cells = (int)cells;
     h->n_act = (int)act;
-    int cap = o.stencil_cap > 0 ? o.stencil_cap : ((int)std::ceil(max_stencil) + 31) / 32 * 32;
+    // staging capacity: the neighbourhood plus one padding slot, a multiple of 32
+    int cap = o.stencil_cap > 0 ? o.stencil_cap : ((int)std::ceil(max_stencil) + 1 + 31) / 32 * 32;
     h->stencil_cap = cap;
-    // warps per block: as many as fit 200 KB of shared memory, at most 4
-    const size_t per_warp = phase_smem_bytes(cap, 1);
-    h->wpb = (int)std::max<size_t>(1, std::min<size_t>(4, (200u * 1024u) / per_warp));
-    if (per_warp > 220u * 1024u) {
+    // warps per cell: spread small grids over more warps so that every SM has
+    // work; large grids keep one warp per cell (enough cells to fill the GPU)
+    if (o.warps_per_cell != 0 && o.warps_per_cell != 1 && o.warps_per_cell != 2 && o.warps_per_cell != 4) {
+        delete h;
+        return fail(MC_ERR_INVALID_ARG, "warps_per_cell must be 0, 1, 2 or 4");
+    }
+    if (o.warps_per_cell > 0) h->wpb = o.warps_per_cell;
+    else h->wpb = h->n_act >= 152 * 12 ? 1 : (h->n_act >= 152 * 3 ? 2 : 4);
+    // raw records of the whole neighbourhood in shared memory when every
+    // attempt needs them (FP64 mode; n_c = 2 boxes), else of the own cell only
+    h->full_rec = (h->precision == MC_PREC_FP64 || any_small) ? 1 : 0;
+    h->own_cap = h->full_rec ? cap : std::max(32, ((int)std::ceil(max_own) + 15) / 16 * 16);
+    h->smem_bytes = phase_smem_bytes(cap, h->full_rec ? cap : h->own_cap, h->wpb);
+    if (h->smem_bytes > 220u * 1024u) {
         delete h;
         return fail(MC_ERR_INVALID_ARG, "stencil capacity too large for shared memory");
     }
@@ -487,6 +512,8 @@ int create_impl(mc_handle **out, int n_rep, const double *L, const int32_t *n_mo
     d.n_cells = h->n_cells;
     d.n_act = h->n_act;
     d.stencil_cap = cap;
+    d.full_rec = h->full_rec;
+    d.own_cap = h->own_cap;
     d.precision = h->precision;
     const int M_tot = h->n_sites / 3;
     int4 *r0, *r1;
@@ -506,7 +533,11 @@ int create_impl(mc_handle **out, int n_rep, const double *L, const int32_t *n_mo
         (rc = h->alloc(&h->obs.kref, M_tot)) || (rc = h->alloc(&h->obs.u0, 3 * (size_t)M_tot)) ||
         (rc = h->alloc(&h->d_fs, h->n_sites)) || (rc = h->alloc(&h->d_fscm, M_tot)) ||
         (rc = h->alloc(&h->d_c2, M_tot)) || (rc = h->alloc(&h->d_q, 6 * 256)) ||
-        (rc = h->alloc(&h->d_obs_out, 3 * (size_t)n_rep))) {
+        (rc = h->alloc(&h->d_obs_out, 3 * (size_t)n_rep)) ||
+        (rc = h->alloc(&h->ds.att_rnd, 2 * (size_t)h->n_sites)) || (rc = h->alloc(&h->d_bar, 2)) ||
+        (rc = h->alloc(&h->d_scan_tot, kMaxPersistentBlocks)) ||
+        (rc = h->precision == MC_PREC_FP64 ? h->alloc(&h->ds.att_thr64, h->n_sites)
+                                           : h->alloc(&h->ds.att_thr32, h->n_sites))) {
         mc_destroy(h);
         return rc;
     }
@@ -540,9 +571,15 @@ int create_impl(mc_handle **out, int n_rep, const double *L, const int32_t *n_mo
         mc_destroy(h);
         return fail(MC_ERR_CUDA, "upload of tables failed");
     }
-    if (phase_set_smem_limit(cap, h->wpb) != 0) {
+    if (phase_set_smem_limit((int)h->smem_bytes) != 0) {
         mc_destroy(h);
         return fail(MC_ERR_CUDA, "cannot reserve shared memory for the sweep kernel");
+    }
+    // sweeps run as one persistent cooperative launch per call unless graphs are asked for
+    if (o.launch_mode != 1) h->pgrid = persistent_grid(h->ds, h->wpb, kMaxPersistentBlocks);
+    if (o.launch_mode == 2 && h->pgrid == 0) {
+        mc_destroy(h);
+        return fail(MC_ERR_INVALID_ARG, "persistent sweeps need cooperative launch support");
     }
     std::vector<int4> rec;
     rc = pack_records(h, xyz, nullptr, types, rec);
@@ -602,10 +639,20 @@ static int sweep_impl(mc_handle *h, int n_sweeps, const double *T, const mc_move
     if (rc) return rc;
     if ((rc = set_device(h))) return rc;
     if ((rc = upload_params(h, T, mix, seeds, same))) return rc;
-    for (int s = 0; s < n_sweeps; ++s) {
-        if ((rc = ensure_graph(h, h->cur))) return rc;
-        CUDA_TRY(cudaGraphLaunch(h->graph[h->cur], h->stream));
-        h->cur ^= 1;
+    if (n_sweeps == 0) return MC_OK;
+    if (h->pgrid > 0) {
+        // all sweeps of the call in one cooperative launch (which expects zero
+        // cell counts on entry and leaves them zero)
+        CUDA_TRY(cudaMemsetAsync(h->ds.cell_count, 0, sizeof(int) * h->n_cells, h->stream));
+        const int e = launch_persistent(h->ds, h->cur, n_sweeps, h->wpb, h->pgrid, h->d_bar, h->d_scan_tot, h->stream);
+        if (e != 0) return fail(MC_ERR_CUDA, std::string("persistent sweep launch: ") + cudaGetErrorString((cudaError_t)e));
+        h->cur ^= (n_sweeps & 1);
+    } else {
+        for (int s = 0; s < n_sweeps; ++s) {
+            if ((rc = ensure_graph(h, h->cur))) return rc;
+            CUDA_TRY(cudaGraphLaunch(h->graph[h->cur], h->stream));
+            h->cur ^= 1;
+        }
     }
     CUDA_TRY(cudaGetLastError());
     return MC_OK;
@@ -909,6 +956,10 @@ int mc_get_info(mc_handle *h, mc_info *info)
     for (auto &r : h->reps) mx = std::max(mx, r.nc);
     info->max_cells_per_axis = mx;
     info->recheck_gap = h->recheck_gap;
+    info->warps_per_cell = h->wpb;
+    info->active_cells_per_colour = h->n_act;
+    info->launch_mode = h->pgrid > 0 ? 2 : 1;
+    info->persistent_blocks = h->pgrid;
     return MC_OK;
 }
 

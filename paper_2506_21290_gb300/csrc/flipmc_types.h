@@ -77,7 +77,9 @@ struct DevState {
     int n_sites;         // total over replicas
     int n_cells;         // total over replicas
     int n_act;           // active cells per colour, total over replicas
-    int stencil_cap;
+    int stencil_cap;     // atoms staged per neighbourhood (plus one padding slot)
+    int full_rec;        // 1: stage raw records of the whole neighbourhood; 0: own cell only
+    int own_cap;         // raw records staged when full_rec == 0
     int precision;
     const RepInfo *rep;
     const RepParam *par;
@@ -93,6 +95,9 @@ struct DevState {
     int *slot_of;
     int *img;            // 3 per site, indexed by global site index
     double *cell_dE;     // accepted Delta E per cell in the last sweep
+    uint4 *att_rnd;      // 2 per record slot: the 8 random words of the slot's attempt (nullable)
+    float *att_thr32;    // per record slot: FP32 threshold -T ln u (FP32 mode)
+    double *att_thr64;   // per record slot: FP64 threshold (FP64 mode)
     unsigned long long *stats;   // STAT_N per replica
     double *e_run;       // per replica
     int *err;

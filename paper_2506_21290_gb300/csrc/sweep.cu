@@ -1,85 +1,235 @@
 // Checkerboard Metropolis sweep (arXiv 2506.21290 Sec. II.B on a cell grid).
 //
-// One warp owns one active cell of the current colour.  It stages the atoms of
-// the cell and of its neighbour cells (27, or the 8 distinct cells when n_c = 2)
-// in shared memory, draws the random numbers of all its attempts up front
-// (Philox is counter-based: the draws do not depend on the state), then runs
-// the cell's n attempts in order.  Every attempt spreads its candidate atoms
-// over the 32 lanes, reduces Delta E with shuffles, decides, and commits in
-// shared memory; the cell is written back to global memory at the end.
+// A group of W warps (W = 1, 2 or 4) owns one active cell of the current
+// colour.  It stages the atoms of the cell and of its neighbour cells (27, or
+// the 8 distinct cells when n_c = 2) in shared memory and draws the random
+// numbers of its attempts up front (Philox is counter-based: the draws do not
+// depend on the state).  The cell's n attempts then run in rounds: in a round
+// the W warps evaluate W consecutive attempts against the same state, each
+// warp one attempt, and one thread commits them in order.  The commit stops at
+// the first attempt that an earlier accepted attempt of the round could have
+// influenced: same molecule, or an atom of the earlier move (old or new
+// position) within 1.01 times the largest WCA cutoff of an atom of the later
+// one.  Interactions between different molecules are WCA only, so an attempt
+// that passes this test has exactly the Delta E, decision and log entry it
+// would have had after the earlier commit; the uncommitted attempts are
+// evaluated again in the next round.  The chain is therefore the sequential
+// one, for every W.
 //
-// Precision modes:
-//   FP64: every Delta E is the FP64 ordered sum (moved atom ascending, then
-//         partner index ascending) of the nonzero pair terms, evaluated with
-//         unfused round-to-nearest operations; this reproduces the reference
-//         FP64 chain exactly.
-//   FP32: pair terms in FP32 from cell-local coordinates; the Metropolis
-//         comparison against the FP64 threshold -T ln u is retaken in the FP64
-//         ordered sum whenever |dE32 - thr| <= gap * (sum of term magnitudes),
-//         or when a bond comes near its FENE divergence.
+// FP32 mode, one attempt by one warp:
+//   1. candidate pass: each lane takes pairs of candidates from the cell-local
+//      structure-of-arrays coordinates and evaluates old and new squared
+//      distances with packed f32x2 arithmetic (the new one as
+//      r'^2 = r^2 - 2 d.delta + |delta|^2); candidates inside the largest WCA
+//      cutoff, or in the same molecule, are queued in ballot order.
+//   2. interaction pass over the queue: WCA (Eq. 1) and FENE (Eq. 2), old and
+//      new, in FP32, each with a magnitude that bounds its rounding error.
+//   3. decision: |dE32 - thr32| against gap * sum(magnitudes) plus the error
+//      bound of the FP32 threshold -T ln u.  Outside that band the FP32
+//      comparison agrees with the FP64 one; inside it (or near a FENE
+//      divergence, or on a non-finite value) the warp recomputes Delta E and
+//      the threshold in FP64, in the reference order, and decides on those.
+// The FP32 error of a pair term is at most a few 1e-6 of its magnitude
+// 4 eps s^12 + 4 eps s^6 + eps (FENE: K eps (|ln(1-x)| + x/(1-x))): positions
+// are cell-local (|x| < 1.5 cells), so r^2 carries ~5e-7 relative error, s^6 and
+// s^12 ~2e-6 and ~4e-6; gap = 1e-4 leaves a factor of >= 10.
+//
+// FP64 mode: every Delta E is the FP64 ordered sum (moved atom ascending, then
+// partner index ascending) of the nonzero pair terms, each operation unfused
+// and rounded to nearest, and the threshold is the FP64 series logarithm; this
+// reproduces the reference FP64 chain exactly.
 #include <algorithm>
 #include <cstdio>
 
 #include "cell_list.h"
+#include "cell_list_dev.cuh"
 #include "flipmc_device.cuh"
 
 namespace flipmc {
 
-constexpr int TERM_CAP = 192;       // nonzero FP64 terms of one move
+constexpr int TERM_CAP = 128;       // nonzero FP64 terms of one move
+constexpr int QW = 64;              // interaction queue entries per warp
+constexpr int BLOCK = 128;          // threads per block (all W)
 constexpr unsigned FULL = 0xffffffffu;
+constexpr float FAR = 1.0e18f;      // coordinate of the padding candidate
+
+// ---------------------------------------------------------------------------
+// packed FP32 pairs (f32x2, sm_100 and later)
+// ---------------------------------------------------------------------------
+typedef unsigned long long f2_t;
+
+__device__ __forceinline__ f2_t pk(float a, float b)
+{
+    f2_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void upk(f2_t v, float &a, float &b)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ f2_t add2(f2_t a, f2_t b)
+{
+    f2_t r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2_t mul2(f2_t a, f2_t b)
+{
+    f2_t r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2_t fma2(f2_t a, f2_t b, f2_t c)
+{
+    f2_t r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
 
 struct PosF {
     float x, y, z;
 };
 
-// per-warp shared-memory scratch
-struct Scratch {
-    int4 *rec;              // [cap] staged records
-    float4 *pos;            // [cap] cell-local FP32 positions (FP32 mode)
-    unsigned long long *key; // [TERM_CAP]
-    double *val;            // [TERM_CAP]
-    double *sorted;         // [TERM_CAP]
-    uint32_t *rnd;          // [32 * 8]
-    double *thr;            // [32]
-    int *cstart;            // [32]
-    int *coff;              // [32]
-    int *misc;              // [8]
+struct Q3 {
+    uint32_t x, y, z;
 };
 
-__host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+// ---------------------------------------------------------------------------
+// shared memory
+// ---------------------------------------------------------------------------
 
-__host__ __device__ inline size_t scratch_bytes(int cap)
+// per warp: interaction queue, and (aliased, used after it) the FP64 term buffers
+struct WarpScr {
+    int *qc;                    // [QW]
+    float *qr;                  // [6 * QW]
+    unsigned long long *key;    // [TERM_CAP]
+    double *val;                // [TERM_CAP]
+    double *sorted;             // [TERM_CAP]
+    int *cnt;                   // [4]
+};
+
+// the outcome of one evaluated attempt, for the in-order commit
+struct Res {
+    int status, accept, flags, mvt, nmv, site, mol, nat;
+    int ks[3], t3n[3];
+    uint32_t qn[3][3];
+    float px[6], py[6], pz[6];  // atoms of the move (old and new positions), cell-local
+    double dE_used;             // Delta E added to the running energy if accepted
+    double dE_log;              // Delta E as the mode computed it
+    double dE64;
+    float scale;
+    int pairs;                  // site-pair evaluations per candidate (2 or 6)
+};
+
+struct Group {
+    float *sx, *sy, *sz;        // [cap] cell-local FP32 coordinates
+    int *sw;                    // [cap] record words
+    int4 *rec;                  // [cap or own_cap] raw records {qx, qy, qz, w}, own cell first
+    uint32_t *rnd;              // [32 * 8] random words of a chunk of attempts
+    double *thr64;              // [32]
+    float *thr32;               // [32]
+    int *cstart;                // [32]
+    int *coff;                  // [32]
+    int *misc;                  // [16]
+    Res *res;                   // [W]
+    unsigned char *warp_base;   // W per-warp scratch blocks
+};
+
+enum { MS_K = 0, MS_N = 1, MS_START = 2, MS_ADV = 3 };
+
+__host__ __device__ constexpr size_t al16(size_t x) { return (x + 15) & ~size_t(15); }
+
+__host__ __device__ inline size_t warp_scr_bytes()
 {
-    return align16(sizeof(int4) * cap) + align16(sizeof(float4) * cap) +
-           align16(sizeof(unsigned long long) * TERM_CAP) + 2 * align16(sizeof(double) * TERM_CAP) +
-           align16(sizeof(uint32_t) * 256) + align16(sizeof(double) * 32) + 3 * align16(sizeof(int) * 32);
+    const size_t q = al16(sizeof(int) * QW) + al16(sizeof(float) * 6 * QW);
+    const size_t t = al16(sizeof(unsigned long long) * TERM_CAP) + 2 * al16(sizeof(double) * TERM_CAP);
+    return (q > t ? q : t) + al16(sizeof(int) * 4);
 }
 
-__device__ inline Scratch carve(unsigned char *base, int cap)
+__host__ __device__ inline size_t group_bytes(int cap, int rec_cap, int W)
 {
-    Scratch s;
+    return 4 * al16(sizeof(float) * cap) + al16(sizeof(int4) * rec_cap) + al16(sizeof(uint32_t) * 256) +
+           al16(sizeof(double) * 32) + al16(sizeof(float) * 32) + 3 * al16(sizeof(int) * 32) +
+           al16(sizeof(Res) * W) + (size_t)W * warp_scr_bytes();
+}
+
+__device__ inline Group carve(unsigned char *base, int cap, int rec_cap, int W)
+{
+    Group s;
     size_t o = 0;
-    s.rec = (int4 *)(base + o);
-    o += align16(sizeof(int4) * cap);
-    s.pos = (float4 *)(base + o);
-    o += align16(sizeof(float4) * cap);
-    s.key = (unsigned long long *)(base + o);
-    o += align16(sizeof(unsigned long long) * TERM_CAP);
-    s.val = (double *)(base + o);
-    o += align16(sizeof(double) * TERM_CAP);
-    s.sorted = (double *)(base + o);
-    o += align16(sizeof(double) * TERM_CAP);
-    s.rnd = (uint32_t *)(base + o);
-    o += align16(sizeof(uint32_t) * 256);
-    s.thr = (double *)(base + o);
-    o += align16(sizeof(double) * 32);
-    s.cstart = (int *)(base + o);
-    o += align16(sizeof(int) * 32);
-    s.coff = (int *)(base + o);
-    o += align16(sizeof(int) * 32);
-    s.misc = (int *)(base + o);
+    auto take = [&](size_t bytes) {
+        unsigned char *p = base + o;
+        o += al16(bytes);
+        return p;
+    };
+    s.sx = (float *)take(sizeof(float) * cap);
+    s.sy = (float *)take(sizeof(float) * cap);
+    s.sz = (float *)take(sizeof(float) * cap);
+    s.sw = (int *)take(sizeof(int) * cap);
+    s.rec = (int4 *)take(sizeof(int4) * rec_cap);
+    s.rnd = (uint32_t *)take(sizeof(uint32_t) * 256);
+    s.thr64 = (double *)take(sizeof(double) * 32);
+    s.thr32 = (float *)take(sizeof(float) * 32);
+    s.cstart = (int *)take(sizeof(int) * 32);
+    s.coff = (int *)take(sizeof(int) * 32);
+    s.misc = (int *)take(sizeof(int) * 32);
+    s.res = (Res *)take(sizeof(Res) * W);
+    s.warp_base = base + o;
     return s;
 }
+
+__device__ inline WarpScr warp_scr(const Group &G, int wig)
+{
+    unsigned char *b = G.warp_base + (size_t)wig * warp_scr_bytes();
+    WarpScr s;
+    s.qc = (int *)b;
+    s.qr = (float *)(b + al16(sizeof(int) * QW));
+    s.key = (unsigned long long *)b;    // aliases the queue: used only after it
+    s.val = (double *)(b + al16(sizeof(unsigned long long) * TERM_CAP));
+    s.sorted = (double *)(b + al16(sizeof(unsigned long long) * TERM_CAP) + al16(sizeof(double) * TERM_CAP));
+    const size_t q = al16(sizeof(int) * QW) + al16(sizeof(float) * 6 * QW);
+    const size_t t = al16(sizeof(unsigned long long) * TERM_CAP) + 2 * al16(sizeof(double) * TERM_CAP);
+    s.cnt = (int *)(b + (q > t ? q : t));
+    return s;
+}
+
+// barrier over the 32 W threads of one cell group
+template <int W>
+__device__ __forceinline__ void gsync(int gid)
+{
+    if constexpr (W == 1) {
+        __syncwarp();
+    } else {
+        asm volatile("bar.sync %0, %1;" ::"r"(gid + 1), "r"(32 * W) : "memory");
+    }
+}
+
+__device__ __forceinline__ float warp_sum_f(float v)
+{
+    // butterfly: every lane ends with the same bits (each step adds the same pair)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    return v;
+}
+
+// Staged records: the own cell lives in shared memory (it changes during the
+// phase); neighbour cells are read from shared memory when the whole
+// neighbourhood is staged raw, else from global memory (they do not change).
+struct RecView {
+    const int4 *smem;
+    bool full;
+    int n;
+    const int4 *gsrc;
+    const int *cstart, *coff;
+    int ns;
+    __device__ int4 at(int c) const
+    {
+        if (full || c < n) return smem[c];
+        const int k = find_segment(coff, ns, c);
+        return gsrc[cstart[k] + (c - coff[k])];
+    }
+};
 
 // A proposed move, as the FP64 ordered sum needs it.
 struct Move {
@@ -93,39 +243,18 @@ struct Move {
     bool intra;            // rotation: intramolecular pairs change too
 };
 
-__device__ __forceinline__ float r2_loc(const float4 &p, const PosF &s)
-{
-    const float dx = p.x - s.x, dy = p.y - s.y, dz = p.z - s.z;
-    return fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-}
-
-__device__ __forceinline__ float r2_int32f(uint32_t ax, uint32_t ay, uint32_t az, const uint32_t *b, float hf)
-{
-    const float dx = (float)(int)(ax - b[0]) * hf;
-    const float dy = (float)(int)(ay - b[1]) * hf;
-    const float dz = (float)(int)(az - b[2]) * hf;
-    return fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-}
-
-__device__ __forceinline__ float warp_sum_f(float v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
-    return v;
-}
-
 // ---------------------------------------------------------------------------
-// FP64 ordered Delta E of a move (all lanes return the same value).
+// FP64 ordered Delta E of a move, one warp (all lanes return the same value).
 // Returns MC_ST_EVALUATED or MC_ST_BOND_BREAK.
 // ---------------------------------------------------------------------------
-__device__ int dE64_ordered(const Move &mv, const Scratch &ws, int K, const ModelDev &md, double h, float hf,
-                            float pre_r2, int lane, int *err, double &dE)
+__device__ __noinline__ int dE64_ordered(const Move &mv, const RecView &rv, const WarpScr &S, int K, const ModelDev &md,
+                                         double h, float hf, float pre_r2, int lane, int *err, double &dE)
 {
-    if (lane == 0) ws.misc[0] = 0;
+    if (lane == 0) S.cnt[0] = 0;
     __syncwarp();
     int brk = 0;
     for (int c = lane; c < K; c += 32) {
-        const int4 r = ws.rec[c];
+        const int4 r = rv.at(c);
         const int sj = rec_site(r.w);
         bool in_set = false;
         for (int k = 0; k < mv.n; ++k) in_set |= (sj == mv.site[k]);
@@ -153,18 +282,18 @@ __device__ int dE64_ordered(const Move &mv, const Scratch &ws, int K, const Mode
             if (bonded && !(r2n < md.R2[abn])) brk = 1;
             const double term = __dsub_rn(phi64(md, r2n, abn, bonded), phi64(md, r2o, abo, bonded));
             if (term != 0.0) {
-                const int p = atomicAdd(ws.misc, 1);
+                const int p = atomicAdd(S.cnt, 1);
                 if (p < TERM_CAP) {
-                    ws.key[p] = ((unsigned long long)k << 32) | (unsigned)sj;
-                    ws.val[p] = term;
+                    S.key[p] = ((unsigned long long)k << 32) | (unsigned)sj;
+                    S.val[p] = term;
                 }
             }
         }
     }
     if (mv.intra && lane == 0) {
-        const int pk[3] = {0, 0, 1}, pl[3] = {1, 2, 2};
+        const int pk3[3] = {0, 0, 1}, pl3[3] = {1, 2, 2};
         for (int pr = 0; pr < 3; ++pr) {
-            const int k = pk[pr], l = pl[pr];
+            const int k = pk3[pr], l = pl3[pr];
             const int ab = 3 * mv.to[k] + mv.to[l];
             const double r2o = r2_fixed64((int)(mv.qo[l][0] - mv.qo[k][0]), (int)(mv.qo[l][1] - mv.qo[k][1]),
                                           (int)(mv.qo[l][2] - mv.qo[k][2]), h);
@@ -173,204 +302,40 @@ __device__ int dE64_ordered(const Move &mv, const Scratch &ws, int K, const Mode
             if (!(r2n < md.R2[ab])) brk = 1;
             const double term = __dsub_rn(phi64(md, r2n, ab, true), phi64(md, r2o, ab, true));
             if (term != 0.0) {
-                const int p = atomicAdd(ws.misc, 1);
+                const int p = atomicAdd(S.cnt, 1);
                 if (p < TERM_CAP) {
-                    ws.key[p] = (3ull << 32) | (unsigned)pr;
-                    ws.val[p] = term;
+                    S.key[p] = (3ull << 32) | (unsigned)pr;
+                    S.val[p] = term;
                 }
             }
         }
     }
     brk = __any_sync(FULL, brk);
     __syncwarp();
-    const int nt = ws.misc[0];
+    const int nt = S.cnt[0];
     if (nt > TERM_CAP) {
         if (lane == 0) atomicOr(err, ERR_TERMS);
         dE = __longlong_as_double(0x7FF8000000000000ll);
         return MC_ST_EVALUATED;
     }
     for (int e = lane; e < nt; e += 32) {
-        const unsigned long long key = ws.key[e];
+        const unsigned long long key = S.key[e];
         int rank = 0;
-        for (int f = 0; f < nt; ++f) rank += ws.key[f] < key;
-        ws.sorted[rank] = ws.val[e];
+        for (int f = 0; f < nt; ++f) rank += S.key[f] < key;
+        S.sorted[rank] = S.val[e];
     }
     __syncwarp();
     double s = 0.0;
     if (lane == 0)
-        for (int e = 0; e < nt; ++e) s = __dadd_rn(s, ws.sorted[e]);
+        for (int e = 0; e < nt; ++e) s = __dadd_rn(s, S.sorted[e]);
     dE = __shfl_sync(FULL, s, 0);
     __syncwarp();
     return brk ? MC_ST_BOND_BREAK : MC_ST_EVALUATED;
 }
 
-// ---------------------------------------------------------------------------
-// FP32 Delta E loops.  Return (dE, mag, guard) reduced over the warp.
-// SMALL: n_c = 2, candidates are distinct atoms and distances come from the
-// int32 differences; otherwise from the cell-local float coordinates.
-// ---------------------------------------------------------------------------
-struct Acc32 {
-    float dE, mag;
-    int guard;
-};
-
-template <bool SMALL>
-__device__ Acc32 atom_dE32(const Scratch &ws, int K, const ModelDev &md, int wi, int ti, const PosF &so,
-                           const PosF &sn, const uint32_t *qo, const uint32_t *qn, float hf, float rc2max, int lane)
-{
-    const int mol = rec_mol(wi);
-    float dE = 0.f, mag = 0.f;
-    int guard = 0;
-    for (int c = lane; c < K; c += 32) {
-        float r2o, r2n;
-        int wj;
-        if (SMALL) {
-            const int4 r = ws.rec[c];
-            wj = r.w;
-            r2o = r2_int32f((uint32_t)r.x, (uint32_t)r.y, (uint32_t)r.z, qo, hf);
-            r2n = r2_int32f((uint32_t)r.x, (uint32_t)r.y, (uint32_t)r.z, qn, hf);
-        } else {
-            const float4 p = ws.pos[c];
-            wj = __float_as_int(p.w);
-            r2o = r2_loc(p, so);
-            r2n = r2_loc(p, sn);
-        }
-        const bool bonded = rec_mol(wj) == mol;
-        if ((r2o < rc2max || r2n < rc2max || bonded) && wj != wi) {
-            const int ab = 3 * ti + rec_type(wj);
-            float uo = 0.f, mo = 0.f, un = 0.f, mn = 0.f;
-            if (r2o < md.rc2f[ab]) wca32(md, r2o, ab, uo, mo);
-            if (r2n < md.rc2f[ab]) wca32(md, r2n, ab, un, mn);
-            if (bonded) {
-                if (r2n * md.invR2f[ab] >= md.bond_guard_f || r2o * md.invR2f[ab] >= md.bond_guard_f) {
-                    guard = 1;
-                } else {
-                    float fo, fmo, fn, fmn;
-                    fene32(md, r2o, ab, fo, fmo);
-                    fene32(md, r2n, ab, fn, fmn);
-                    uo += fo;
-                    un += fn;
-                    mo += fmo;
-                    mn += fmn;
-                }
-            }
-            dE += un - uo;
-            mag += mo + mn;
-        }
-    }
-    Acc32 a;
-    a.dE = warp_sum_f(dE);
-    a.mag = warp_sum_f(mag);
-    a.guard = __any_sync(FULL, guard);
-    return a;
-}
-
-template <bool SMALL>
-__device__ Acc32 flip_dE32(const Scratch &ws, int K, const ModelDev &md, int mol, int wp2, int wq2, int tp, int tq,
-                           const PosF &sp, const PosF &sq, const uint32_t *qp, const uint32_t *qq, float hf,
-                           float rc2max, int lane)
-{
-    float dE = 0.f, mag = 0.f;
-    int guard = 0;
-    for (int c = lane; c < K; c += 32) {
-        float r2p, r2q;
-        int wj;
-        if (SMALL) {
-            const int4 r = ws.rec[c];
-            wj = r.w;
-            r2p = r2_int32f((uint32_t)r.x, (uint32_t)r.y, (uint32_t)r.z, qp, hf);
-            r2q = r2_int32f((uint32_t)r.x, (uint32_t)r.y, (uint32_t)r.z, qq, hf);
-        } else {
-            const float4 p = ws.pos[c];
-            wj = __float_as_int(p.w);
-            r2p = r2_loc(p, sp);
-            r2q = r2_loc(p, sq);
-        }
-        const int w2 = (int)((uint32_t)wj >> 2);
-        const bool bonded = rec_mol(wj) == mol;
-        if ((r2p < rc2max || r2q < rc2max || bonded) && w2 != wp2 && w2 != wq2) {
-            const int tj = rec_type(wj);
-            // atom p: type tp -> tq; atom q: type tq -> tp
-            const int ab_po = 3 * tp + tj, ab_pn = 3 * tq + tj;
-            const int ab_qo = 3 * tq + tj, ab_qn = 3 * tp + tj;
-            float uo = 0.f, mo = 0.f, un = 0.f, mn = 0.f, u, m;
-            if (r2p < md.rc2f[ab_po]) { wca32(md, r2p, ab_po, u, m); uo += u; mo += m; }
-            if (r2p < md.rc2f[ab_pn]) { wca32(md, r2p, ab_pn, u, m); un += u; mn += m; }
-            if (r2q < md.rc2f[ab_qo]) { wca32(md, r2q, ab_qo, u, m); uo += u; mo += m; }
-            if (r2q < md.rc2f[ab_qn]) { wca32(md, r2q, ab_qn, u, m); un += u; mn += m; }
-            if (bonded) {
-                const float g = md.bond_guard_f;
-                if (r2p * md.invR2f[ab_po] >= g || r2p * md.invR2f[ab_pn] >= g || r2q * md.invR2f[ab_qo] >= g ||
-                    r2q * md.invR2f[ab_qn] >= g) {
-                    guard = 1;
-                } else {
-                    fene32(md, r2p, ab_po, u, m); uo += u; mo += m;
-                    fene32(md, r2p, ab_pn, u, m); un += u; mn += m;
-                    fene32(md, r2q, ab_qo, u, m); uo += u; mo += m;
-                    fene32(md, r2q, ab_qn, u, m); un += u; mn += m;
-                }
-            }
-            dE += un - uo;
-            mag += mo + mn;
-        }
-    }
-    Acc32 a;
-    a.dE = warp_sum_f(dE);
-    a.mag = warp_sum_f(mag);
-    a.guard = __any_sync(FULL, guard);
-    return a;
-}
-
-template <bool SMALL>
-__device__ Acc32 mol_dE32(const Scratch &ws, int K, const ModelDev &md, int mol, const int *t3, const PosF *so,
-                          const PosF *sn, const uint32_t (*qo)[3], const uint32_t (*qn)[3], float hf, float rc2max,
-                          int lane)
-{
-    float dE = 0.f, mag = 0.f;
-    for (int c = lane; c < K; c += 32) {
-        float r2o[3], r2n[3];
-        int wj;
-        if (SMALL) {
-            const int4 r = ws.rec[c];
-            wj = r.w;
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                r2o[k] = r2_int32f((uint32_t)r.x, (uint32_t)r.y, (uint32_t)r.z, qo[k], hf);
-                r2n[k] = r2_int32f((uint32_t)r.x, (uint32_t)r.y, (uint32_t)r.z, qn[k], hf);
-            }
-        } else {
-            const float4 p = ws.pos[c];
-            wj = __float_as_int(p.w);
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                r2o[k] = r2_loc(p, so[k]);
-                r2n[k] = r2_loc(p, sn[k]);
-            }
-        }
-        if (rec_mol(wj) == mol) continue;
-        bool near = false;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) near |= (r2o[k] < rc2max) | (r2n[k] < rc2max);
-        if (!near) continue;
-        const int tj = rec_type(wj);
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            const int ab = 3 * t3[k] + tj;
-            float u, m;
-            if (r2o[k] < md.rc2f[ab]) { wca32(md, r2o[k], ab, u, m); dE -= u; mag += m; }
-            if (r2n[k] < md.rc2f[ab]) { wca32(md, r2n[k], ab, u, m); dE += u; mag += m; }
-        }
-    }
-    Acc32 a;
-    a.dE = warp_sum_f(dE);
-    a.mag = warp_sum_f(mag);
-    a.guard = 0;
-    return a;
-}
-
 // Rotation proposal about the centroid (FP64, unfused, the reference order).
-__device__ void rotate_molecule(const uint32_t (*q)[3], uint32_t (*qn)[3], const uint32_t *w3, double rot_a, double h,
-                                double inv_h)
+__device__ __noinline__ void rotate_molecule(const uint32_t (*q)[3], uint32_t (*qn)[3], const uint32_t *w3,
+                                             double rot_a, double h, double inv_h)
 {
     double rel[3][3], cen[3];
     for (int k = 0; k < 3; ++k)
@@ -409,30 +374,615 @@ __device__ void rotate_molecule(const uint32_t (*q)[3], uint32_t (*qn)[3], const
 }
 
 // ---------------------------------------------------------------------------
+// FP32 candidate passes: fill the warp's interaction queue
+// ---------------------------------------------------------------------------
+
+// warp-aggregated append, ballot order; entries past QW are counted but not
+// stored (the caller then decides in FP64).  r2 value j of entry e is qr[j*QW+e].
+template <int NV>
+__device__ __forceinline__ void push2(const WarpScr &S, int lane, int &qlen, bool p0, int c0, const float *v0, bool p1,
+                                      int c1, const float *v1)
+{
+    const unsigned b0 = __ballot_sync(FULL, p0), b1 = __ballot_sync(FULL, p1);
+    const int base = qlen;
+    qlen += __popc(b0) + __popc(b1);
+    const unsigned lt = (1u << lane) - 1u;
+    if (p0) {
+        const int e = base + __popc(b0 & lt);
+        if (e < QW) {
+            S.qc[e] = c0;
+#pragma unroll
+            for (int j = 0; j < NV; ++j) S.qr[j * QW + e] = v0[j];
+        }
+    }
+    if (p1) {
+        const int e = base + __popc(b0) + __popc(b1 & lt);
+        if (e < QW) {
+            S.qc[e] = c1;
+#pragma unroll
+            for (int j = 0; j < NV; ++j) S.qr[j * QW + e] = v1[j];
+        }
+    }
+}
+
+__device__ __forceinline__ float r2_int32f(const int4 &r, const Q3 b, float hf)
+{
+    const float dx = (float)(int)((uint32_t)r.x - b.x) * hf;
+    const float dy = (float)(int)((uint32_t)r.y - b.y) * hf;
+    const float dz = (float)(int)((uint32_t)r.z - b.z) * hf;
+    return fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+}
+
+// Atom translation: old and new distance to every candidate.
+__device__ __forceinline__ int pass_atom(const Group &G, const WarpScr &S, int K, int lane, bool small, const PosF so,
+                                         const PosF sn, int wi, const Q3 qo, const Q3 qn, float hf, float rc2max)
+{
+    int qlen = 0;
+    if (!small) {
+        const float dx = sn.x - so.x, dy = sn.y - so.y, dz = sn.z - so.z;
+        const f2_t nxo = pk(-so.x, -so.x), nyo = pk(-so.y, -so.y), nzo = pk(-so.z, -so.z);
+        const f2_t mx = pk(-2.f * dx, -2.f * dx), my = pk(-2.f * dy, -2.f * dy), mz = pk(-2.f * dz, -2.f * dz);
+        const float dd = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        const f2_t d2 = pk(dd, dd);
+        for (int base = 0; base < K; base += 64) {
+            const int c = base + 2 * lane;
+            bool p0 = false, p1 = false;
+            float v0[2] = {0.f, 0.f}, v1[2] = {0.f, 0.f};
+            if (c < K) {
+                const f2_t X = *(const f2_t *)(G.sx + c);
+                const f2_t Y = *(const f2_t *)(G.sy + c);
+                const f2_t Z = *(const f2_t *)(G.sz + c);
+                const int2 ww = *(const int2 *)(G.sw + c);
+                const f2_t ex = add2(X, nxo), ey = add2(Y, nyo), ez = add2(Z, nzo);
+                const f2_t r2o = fma2(ez, ez, fma2(ey, ey, mul2(ex, ex)));
+                const f2_t r2n = fma2(ez, mz, fma2(ey, my, fma2(ex, mx, add2(r2o, d2))));
+                upk(r2o, v0[0], v1[0]);
+                upk(r2n, v0[1], v1[1]);
+                p0 = (fminf(v0[0], v0[1]) < rc2max) | ((ww.x ^ wi) < 16);
+                p1 = (fminf(v1[0], v1[1]) < rc2max) | ((ww.y ^ wi) < 16);
+            }
+            push2<2>(S, lane, qlen, p0, c, v0, p1, c + 1, v1);
+        }
+    } else {
+        for (int base = 0; base < K; base += 64) {
+            const int c = base + 2 * lane;
+            bool p0 = false, p1 = false;
+            float v0[2] = {0.f, 0.f}, v1[2] = {0.f, 0.f};
+            if (c < K) {
+                const int4 r = G.rec[c];
+                v0[0] = r2_int32f(r, qo, hf);
+                v0[1] = r2_int32f(r, qn, hf);
+                p0 = (fminf(v0[0], v0[1]) < rc2max) | ((r.w ^ wi) < 16);
+            }
+            if (c + 1 < K) {
+                const int4 r = G.rec[c + 1];
+                v1[0] = r2_int32f(r, qo, hf);
+                v1[1] = r2_int32f(r, qn, hf);
+                p1 = (fminf(v1[0], v1[1]) < rc2max) | ((r.w ^ wi) < 16);
+            }
+            push2<2>(S, lane, qlen, p0, c, v0, p1, c + 1, v1);
+        }
+    }
+    return qlen;
+}
+
+// Flip: distance of every candidate to the two atoms whose types swap.
+__device__ __forceinline__ int pass_flip(const Group &G, const WarpScr &S, int K, int lane, bool small, const PosF sp,
+                                         const PosF sq, int wi, const Q3 qp, const Q3 qq, float hf, float rc2max)
+{
+    int qlen = 0;
+    if (!small) {
+        const f2_t npx = pk(-sp.x, -sp.x), npy = pk(-sp.y, -sp.y), npz = pk(-sp.z, -sp.z);
+        const f2_t nqx = pk(-sq.x, -sq.x), nqy = pk(-sq.y, -sq.y), nqz = pk(-sq.z, -sq.z);
+        for (int base = 0; base < K; base += 64) {
+            const int c = base + 2 * lane;
+            bool p0 = false, p1 = false;
+            float v0[2] = {0.f, 0.f}, v1[2] = {0.f, 0.f};
+            if (c < K) {
+                const f2_t X = *(const f2_t *)(G.sx + c);
+                const f2_t Y = *(const f2_t *)(G.sy + c);
+                const f2_t Z = *(const f2_t *)(G.sz + c);
+                const int2 ww = *(const int2 *)(G.sw + c);
+                f2_t ex = add2(X, npx), ey = add2(Y, npy), ez = add2(Z, npz);
+                const f2_t rp = fma2(ez, ez, fma2(ey, ey, mul2(ex, ex)));
+                ex = add2(X, nqx);
+                ey = add2(Y, nqy);
+                ez = add2(Z, nqz);
+                const f2_t rq = fma2(ez, ez, fma2(ey, ey, mul2(ex, ex)));
+                upk(rp, v0[0], v1[0]);
+                upk(rq, v0[1], v1[1]);
+                p0 = (fminf(v0[0], v0[1]) < rc2max) | ((ww.x ^ wi) < 16);
+                p1 = (fminf(v1[0], v1[1]) < rc2max) | ((ww.y ^ wi) < 16);
+            }
+            push2<2>(S, lane, qlen, p0, c, v0, p1, c + 1, v1);
+        }
+    } else {
+        for (int base = 0; base < K; base += 64) {
+            const int c = base + 2 * lane;
+            bool p0 = false, p1 = false;
+            float v0[2] = {0.f, 0.f}, v1[2] = {0.f, 0.f};
+            if (c < K) {
+                const int4 r = G.rec[c];
+                v0[0] = r2_int32f(r, qp, hf);
+                v0[1] = r2_int32f(r, qq, hf);
+                p0 = (fminf(v0[0], v0[1]) < rc2max) | ((r.w ^ wi) < 16);
+            }
+            if (c + 1 < K) {
+                const int4 r = G.rec[c + 1];
+                v1[0] = r2_int32f(r, qp, hf);
+                v1[1] = r2_int32f(r, qq, hf);
+                p1 = (fminf(v1[0], v1[1]) < rc2max) | ((r.w ^ wi) < 16);
+            }
+            push2<2>(S, lane, qlen, p0, c, v0, p1, c + 1, v1);
+        }
+    }
+    return qlen;
+}
+
+// Rigid molecule move: old and new distances of the three atoms.
+__device__ __noinline__ int pass_mol(const Group &G, const WarpScr &S, int K, int lane, bool small, const PosF *so,
+                                     const PosF *sn, int wi, const Q3 *qo, const Q3 *qn, float hf, float rc2max)
+{
+    int qlen = 0;
+    for (int base = 0; base < K; base += 64) {
+        bool pp[2] = {false, false};
+        float v[2][6];
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+            const int c = base + 2 * lane + hh;
+#pragma unroll
+            for (int j = 0; j < 6; ++j) v[hh][j] = 0.f;
+            if (c < K) {
+                int w;
+                if (small) {
+                    const int4 r = G.rec[c];
+                    w = r.w;
+#pragma unroll
+                    for (int s = 0; s < 3; ++s) {
+                        v[hh][s] = r2_int32f(r, qo[s], hf);
+                        v[hh][3 + s] = r2_int32f(r, qn[s], hf);
+                    }
+                } else {
+                    const float x = G.sx[c], y = G.sy[c], z = G.sz[c];
+                    w = G.sw[c];
+#pragma unroll
+                    for (int s = 0; s < 3; ++s) {
+                        float ex = x - so[s].x, ey = y - so[s].y, ez = z - so[s].z;
+                        v[hh][s] = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+                        ex = x - sn[s].x;
+                        ey = y - sn[s].y;
+                        ez = z - sn[s].z;
+                        v[hh][3 + s] = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+                    }
+                }
+                float mn = v[hh][0];
+#pragma unroll
+                for (int j = 1; j < 6; ++j) mn = fminf(mn, v[hh][j]);
+                pp[hh] = (mn < rc2max) && ((w ^ wi) >= 16);
+            }
+        }
+        push2<6>(S, lane, qlen, pp[0], base + 2 * lane, v[0], pp[1], base + 2 * lane + 1, v[1]);
+    }
+    return qlen;
+}
+
+// ---------------------------------------------------------------------------
+// FP32 interaction passes over the queue: partial (dE, mag, guard) per lane
+// ---------------------------------------------------------------------------
+struct Acc32 {
+    float dE, mag;
+    int guard;
+};
+
+__device__ __forceinline__ void add_wca(const ModelDev &md, float r2, int ab, float sign, Acc32 &a)
+{
+    if (r2 < md.rc2f[ab]) {
+        float u, m;
+        wca32(md, r2, ab, u, m);
+        a.dE = fmaf(sign, u, a.dE);
+        a.mag += m;
+    }
+}
+
+__device__ __forceinline__ void add_fene(const ModelDev &md, float r2, int ab, float sign, Acc32 &a)
+{
+    if (r2 * md.invR2f[ab] >= md.bond_guard_f) {
+        a.guard = 1;
+        return;
+    }
+    float u, m;
+    fene32(md, r2, ab, u, m);
+    a.dE = fmaf(sign, u, a.dE);
+    a.mag += m;
+}
+
+__device__ __forceinline__ Acc32 inter_atom(const Group &G, const WarpScr &S, int nq, int lane, const ModelDev &md,
+                                            int k, int wi, int ti)
+{
+    Acc32 a{0.f, 0.f, 0};
+    for (int e = lane; e < nq; e += 32) {
+        const int c = S.qc[e];
+        if (c == k) continue;
+        const int wj = G.sw[c];
+        const int ab = 3 * ti + rec_type(wj);
+        const float r2o = S.qr[e], r2n = S.qr[QW + e];
+        add_wca(md, r2o, ab, -1.f, a);
+        add_wca(md, r2n, ab, 1.f, a);
+        if ((wj ^ wi) < 16) {
+            add_fene(md, r2o, ab, -1.f, a);
+            add_fene(md, r2n, ab, 1.f, a);
+        }
+    }
+    return a;
+}
+
+__device__ __forceinline__ Acc32 inter_flip(const Group &G, const WarpScr &S, int nq, int lane, const ModelDev &md,
+                                            int kp, int kq, int wi, int tp, int tq)
+{
+    Acc32 a{0.f, 0.f, 0};
+    for (int e = lane; e < nq; e += 32) {
+        const int c = S.qc[e];
+        if (c == kp || c == kq) continue;
+        const int wj = G.sw[c];
+        const int tj = rec_type(wj);
+        const float rp = S.qr[e], rq = S.qr[QW + e];
+        // atom p: type tp -> tq; atom q: type tq -> tp
+        add_wca(md, rp, 3 * tp + tj, -1.f, a);
+        add_wca(md, rp, 3 * tq + tj, 1.f, a);
+        add_wca(md, rq, 3 * tq + tj, -1.f, a);
+        add_wca(md, rq, 3 * tp + tj, 1.f, a);
+        if ((wj ^ wi) < 16) {
+            add_fene(md, rp, 3 * tp + tj, -1.f, a);
+            add_fene(md, rp, 3 * tq + tj, 1.f, a);
+            add_fene(md, rq, 3 * tq + tj, -1.f, a);
+            add_fene(md, rq, 3 * tp + tj, 1.f, a);
+        }
+    }
+    return a;
+}
+
+__device__ __noinline__ Acc32 inter_mol(const Group &G, const WarpScr &S, int nq, int lane, const ModelDev &md,
+                                        const int *t3)
+{
+    Acc32 a{0.f, 0.f, 0};
+    for (int e = lane; e < nq; e += 32) {
+        const int c = S.qc[e];
+        const int tj = rec_type(G.sw[c]);
+#pragma unroll
+        for (int s = 0; s < 3; ++s) {
+            const int ab = 3 * t3[s] + tj;
+            add_wca(md, S.qr[s * QW + e], ab, -1.f, a);
+            add_wca(md, S.qr[(3 + s) * QW + e], ab, 1.f, a);
+        }
+    }
+    return a;
+}
+
+// intramolecular terms of a rotation (FP32, one lane)
+__device__ __noinline__ void rot_intra32(const ModelDev &md, const Q3 *qo, const Q3 *qn, const int *t3, float hf,
+                                         Acc32 &part)
+{
+    const int pk3[3] = {0, 0, 1}, pl3[3] = {1, 2, 2};
+    for (int pr = 0; pr < 3; ++pr) {
+        const int kk = pk3[pr], ll = pl3[pr];
+        const int ab = 3 * t3[kk] + t3[ll];
+        const int4 ro = make_int4((int)qo[ll].x, (int)qo[ll].y, (int)qo[ll].z, 0);
+        const int4 rn = make_int4((int)qn[ll].x, (int)qn[ll].y, (int)qn[ll].z, 0);
+        const float r2o = r2_int32f(ro, qo[kk], hf);
+        const float r2n = r2_int32f(rn, qn[kk], hf);
+        add_wca(md, r2o, ab, -1.f, part);
+        add_wca(md, r2n, ab, 1.f, part);
+        add_fene(md, r2o, ab, -1.f, part);
+        add_fene(md, r2n, ab, 1.f, part);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Everything one attempt needs that is the same for all attempts of the cell
+// ---------------------------------------------------------------------------
+struct CellCtx {
+    const ModelDev *md;
+    const MixDev *mx;
+    RecView rv;
+    int K, n, cellL, nc;
+    bool small;
+    uint32_t P[3];          // cell centre (fixed point): origin of the cell-local frame
+    uint32_t shift[3];
+    uint64_t sweep, seed;
+    double h, inv_h, T64;
+    float hf, rc2max, pre_r2, gap, T32;
+    int32_t D_atom, D_mol;
+    int *err;
+};
+
+__device__ __forceinline__ PosF local_of(const CellCtx &c, uint32_t x, uint32_t y, uint32_t z)
+{
+    PosF p;
+    p.x = (float)(int)(x - c.P[0]) * c.hf;
+    p.y = (float)(int)(y - c.P[1]) * c.hf;
+    p.z = (float)(int)(z - c.P[2]) * c.hf;
+    return p;
+}
+
+// Evaluate attempt `jr` of the current chunk (one warp, state read-only) and
+// leave its outcome in R (written by lane 0).
+template <int PREC, int W>
+__device__ void evaluate(const CellCtx &cx, const Group &G, const WarpScr &S, Res *R, int jr, int lane)
+{
+    const ModelDev &md = *cx.md;
+    const uint32_t *w = G.rnd + 8 * jr;
+    const int n = cx.n, K = cx.K;
+    const int k = (int)(((unsigned long long)w[0] * (unsigned long long)n) >> 32);
+    const int4 rk = G.rec[k];
+    const int wi = rk.w;
+    const int mol = rec_mol(wi);
+    const int mvt = move_type(w[1], *cx.mx);
+    int status = MC_ST_EVALUATED;
+    int flags = 0, accept = 0;
+    float scale = 0.f;
+    double dE_log = 0.0, dE64 = __longlong_as_double(0x7FF8000000000000ll), used = 0.0;
+
+    int ks[3] = {k, -1, -1};
+    Q3 qo[3], qn[3];
+    int t3o[3] = {0, 0, 0}, t3n[3] = {0, 0, 0};
+    int nmv = 1;
+    if (mvt == MC_MOVE_ATOM) {
+        qo[0] = Q3{(uint32_t)rk.x, (uint32_t)rk.y, (uint32_t)rk.z};
+        qn[0] = Q3{qo[0].x + (uint32_t)uniform_disp(w[4], cx.D_atom), qo[0].y + (uint32_t)uniform_disp(w[5], cx.D_atom),
+                   qo[0].z + (uint32_t)uniform_disp(w[6], cx.D_atom)};
+        t3o[0] = t3n[0] = rec_type(wi);
+        if (cell_local(qn[0].x, qn[0].y, qn[0].z, cx.shift, cx.nc) != cx.cellL) status = MC_ST_LEFT_CELL;
+    } else {
+        // the molecule's atoms in the own cell
+        int k0 = -1, k1 = -1, k2 = -1;
+        for (int j = 0; j < n; ++j) {
+            const int wj = G.rec[j].w;
+            if (rec_mol(wj) == mol) {
+                const int sl = rec_slot(wj);
+                if (sl == 0) k0 = j;
+                if (sl == 1) k1 = j;
+                if (sl == 2) k2 = j;
+            }
+        }
+        if (mvt == MC_MOVE_FLIP) {
+            const int axis = (int)(((unsigned long long)w[7] * 3ull) >> 32);
+            const int kp = axis == 0 ? k1 : k0, kq = axis == 2 ? k1 : k2;
+            if (kp < 0 || kq < 0) {
+                status = MC_ST_NOT_IN_CELL;
+            } else {
+                nmv = 2;
+                ks[0] = kp;
+                ks[1] = kq;
+                const int4 rp = G.rec[kp], rq = G.rec[kq];
+                qo[0] = qn[0] = Q3{(uint32_t)rp.x, (uint32_t)rp.y, (uint32_t)rp.z};
+                qo[1] = qn[1] = Q3{(uint32_t)rq.x, (uint32_t)rq.y, (uint32_t)rq.z};
+                t3o[0] = rec_type(rp.w);
+                t3o[1] = rec_type(rq.w);
+                t3n[0] = t3o[1];
+                t3n[1] = t3o[0];
+            }
+        } else {
+            ks[0] = k0;
+            ks[1] = k1;
+            ks[2] = k2;
+            if (k0 < 0 || k1 < 0 || k2 < 0) {
+                status = MC_ST_NOT_IN_CELL;
+            } else {
+                nmv = 3;
+#pragma unroll
+                for (int s = 0; s < 3; ++s) {
+                    const int4 rs = G.rec[ks[s]];
+                    qo[s] = Q3{(uint32_t)rs.x, (uint32_t)rs.y, (uint32_t)rs.z};
+                    t3o[s] = t3n[s] = rec_type(rs.w);
+                }
+                if (mvt == MC_MOVE_MOL_TRANS) {
+                    const int32_t dx = uniform_disp(w[4], cx.D_mol), dy = uniform_disp(w[5], cx.D_mol),
+                                  dz = uniform_disp(w[6], cx.D_mol);
+#pragma unroll
+                    for (int s = 0; s < 3; ++s)
+                        qn[s] = Q3{qo[s].x + (uint32_t)dx, qo[s].y + (uint32_t)dy, qo[s].z + (uint32_t)dz};
+                } else {
+                    uint32_t a9[9];
+                    if (lane == 0) {
+                        uint32_t qq[3][3], qr[3][3];
+                        for (int s = 0; s < 3; ++s) {
+                            qq[s][0] = qo[s].x;
+                            qq[s][1] = qo[s].y;
+                            qq[s][2] = qo[s].z;
+                        }
+                        rotate_molecule(qq, qr, w + 4, cx.mx->rot_a, cx.h, cx.inv_h);
+                        for (int s = 0; s < 3; ++s)
+                            for (int ax = 0; ax < 3; ++ax) a9[3 * s + ax] = qr[s][ax];
+                    }
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) a9[i] = __shfl_sync(FULL, a9[i], 0);
+#pragma unroll
+                    for (int s = 0; s < 3; ++s) qn[s] = Q3{a9[3 * s], a9[3 * s + 1], a9[3 * s + 2]};
+                }
+#pragma unroll
+                for (int s = 0; s < 3; ++s)
+                    if (cell_local(qn[s].x, qn[s].y, qn[s].z, cx.shift, cx.nc) != cx.cellL) status = MC_ST_LEFT_CELL;
+            }
+        }
+    }
+
+    // the FP64 ordered sum of this move and its decision (-1: bond break)
+    auto exact = [&](double thr) {
+        Move mv;
+        mv.n = nmv;
+        mv.mol = mol;
+        mv.moves_pos = mvt != MC_MOVE_FLIP;
+        mv.intra = mvt == MC_MOVE_MOL_ROT;
+#pragma unroll
+        for (int s = 0; s < 3; ++s) {
+            mv.site[s] = s < nmv ? rec_site(G.rec[ks[s]].w) : -1;
+            mv.to[s] = t3o[s];
+            mv.tn[s] = t3n[s];
+            mv.qo[s][0] = qo[s].x;
+            mv.qo[s][1] = qo[s].y;
+            mv.qo[s][2] = qo[s].z;
+            mv.qn[s][0] = qn[s].x;
+            mv.qn[s][1] = qn[s].y;
+            mv.qn[s][2] = qn[s].z;
+        }
+        double e64 = 0.0;
+        const int st = dE64_ordered(mv, cx.rv, S, K, md, cx.h, cx.hf, cx.pre_r2, lane, cx.err, e64);
+        dE64 = e64;
+        return (st == MC_ST_EVALUATED) ? ((e64 <= thr) ? 1 : 0) : -1;
+    };
+
+    if (status == MC_ST_EVALUATED) {
+        if (PREC == MC_PREC_FP64) {
+            const int dec = exact(G.thr64[jr]);
+            if (dec < 0) status = MC_ST_BOND_BREAK;
+            accept = dec == 1;
+            dE_log = used = dE64;
+        } else {
+            const float thr32 = G.thr32[jr];
+            int qlen;
+            if (mvt == MC_MOVE_ATOM) {
+                const PosF so = PosF{G.sx[k], G.sy[k], G.sz[k]};
+                const PosF sn = local_of(cx, qn[0].x, qn[0].y, qn[0].z);
+                qlen = pass_atom(G, S, K, lane, cx.small, so, sn, wi, qo[0], qn[0], cx.hf, cx.rc2max);
+            } else if (mvt == MC_MOVE_FLIP) {
+                const PosF sp = PosF{G.sx[ks[0]], G.sy[ks[0]], G.sz[ks[0]]};
+                const PosF sq = PosF{G.sx[ks[1]], G.sy[ks[1]], G.sz[ks[1]]};
+                qlen = pass_flip(G, S, K, lane, cx.small, sp, sq, wi, qo[0], qo[1], cx.hf, cx.rc2max);
+            } else {
+                // copies: the helpers below take addresses, the hot path's registers stay registers
+                PosF so[3], sn[3];
+                const Q3 mo[3] = {qo[0], qo[1], qo[2]}, mn[3] = {qn[0], qn[1], qn[2]};
+#pragma unroll
+                for (int s = 0; s < 3; ++s) {
+                    so[s] = PosF{G.sx[ks[s]], G.sy[ks[s]], G.sz[ks[s]]};
+                    sn[s] = local_of(cx, qn[s].x, qn[s].y, qn[s].z);
+                }
+                qlen = pass_mol(G, S, K, lane, cx.small, so, sn, wi, mo, mn, cx.hf, cx.rc2max);
+            }
+            __syncwarp();
+            const int nq = min(qlen, QW);
+            Acc32 part;
+            if (mvt == MC_MOVE_ATOM) {
+                part = inter_atom(G, S, nq, lane, md, k, wi, t3o[0]);
+            } else if (mvt == MC_MOVE_FLIP) {
+                part = inter_flip(G, S, nq, lane, md, ks[0], ks[1], wi, t3o[0], t3o[1]);
+            } else {
+                const int tm[3] = {t3o[0], t3o[1], t3o[2]};
+                part = inter_mol(G, S, nq, lane, md, tm);
+                if (mvt == MC_MOVE_MOL_ROT && lane == 0) {
+                    const Q3 ro[3] = {qo[0], qo[1], qo[2]}, rn[3] = {qn[0], qn[1], qn[2]};
+                    rot_intra32(md, ro, rn, tm, cx.hf, part);
+                }
+            }
+            if (qlen > QW) part.guard = 1;
+            const float dE32 = warp_sum_f(part.dE);
+            const float mag = warp_sum_f(part.mag);
+            const int guard = __any_sync(FULL, part.guard);
+            dE_log = used = (double)dE32;
+            scale = mag;
+            const float diff = fabsf(dE32 - thr32);
+            const float marg = cx.gap * mag + 1e-6f * (cx.T32 + fabsf(thr32) + fabsf(dE32));
+            if (guard || !(diff > marg)) {
+                // retake in FP64: exact Delta E against the exact threshold
+                flags = 1;
+                __syncwarp();
+                const unsigned long long u52 = ((unsigned long long)w[2] << 20) | (unsigned long long)(w[3] >> 12);
+                const double u = __dmul_rn((double)(2ull * u52 + 1ull), 0x1p-53);
+                const double thr = -__dmul_rn(cx.T64, ln_series(u));
+                const int dec = exact(thr);
+                if (dec < 0) status = MC_ST_BOND_BREAK;
+                accept = dec == 1;
+                used = dE64;
+            } else {
+                accept = dE32 <= thr32;
+            }
+        }
+    }
+
+    if (lane == 0) {
+        R->status = status;
+        R->accept = accept;
+        R->flags = flags;
+        R->mvt = mvt;
+        R->nmv = nmv;
+        R->site = rec_site(wi);
+        R->mol = mol;
+        R->dE_used = used;
+        R->dE_log = dE_log;
+        R->dE64 = dE64;
+        R->scale = scale;
+        R->pairs = (mvt == MC_MOVE_MOL_TRANS || mvt == MC_MOVE_MOL_ROT) ? 6 : 2;
+        int na = 0;
+        for (int s = 0; s < 3; ++s) {
+            R->ks[s] = ks[s];
+            R->t3n[s] = t3n[s];
+            R->qn[s][0] = qn[s].x;
+            R->qn[s][1] = qn[s].y;
+            R->qn[s][2] = qn[s].z;
+        }
+        // positions the move reads or writes, for the conflict test of the commit
+        // (one warp per cell: no later attempt of the round to protect)
+        if (W > 1 && status == MC_ST_EVALUATED) {
+            for (int s = 0; s < nmv; ++s) {
+                const PosF a = PosF{G.sx[ks[s]], G.sy[ks[s]], G.sz[ks[s]]};
+                R->px[na] = a.x; R->py[na] = a.y; R->pz[na] = a.z; ++na;
+                if (mvt != MC_MOVE_FLIP) {
+                    const PosF b = local_of(cx, qn[s].x, qn[s].y, qn[s].z);
+                    R->px[na] = b.x; R->py[na] = b.y; R->pz[na] = b.z; ++na;
+                }
+            }
+        }
+        R->nat = na;
+    }
+}
+
+// Could accepted move A (committed earlier in the round) have changed the
+// evaluation of B?  Same molecule, or atoms within 1.01 x the largest cutoff.
+__device__ __forceinline__ bool conflicts(const Res &A, const Res &B, float rconf2)
+{
+    if (A.mol == B.mol) return true;
+    for (int i = 0; i < A.nat; ++i)
+        for (int j = 0; j < B.nat; ++j) {
+            const float dx = A.px[i] - B.px[j], dy = A.py[i] - B.py[j], dz = A.pz[i] - B.pz[j];
+            if (dx * dx + dy * dy + dz * dz < rconf2) return true;
+        }
+    return false;
+}
+
+// ---------------------------------------------------------------------------
 // The phase kernel
 // ---------------------------------------------------------------------------
-template <int PREC>
-__global__ void __launch_bounds__(128) phase_kernel(DevState d, int buf, int colour, LogArgs lg)
-{
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ ModelDev md;
-    __shared__ MixDev mx;
-    {
-        const int *src = (const int *)d.model;
-        int *dst = (int *)&md;
-        for (int i = threadIdx.x; i < (int)(sizeof(ModelDev) / 4); i += blockDim.x) dst[i] = src[i];
-        const int *src2 = (const int *)d.mix;
-        int *dst2 = (int *)&mx;
-        for (int i = threadIdx.x; i < (int)(sizeof(MixDev) / 4); i += blockDim.x) dst2[i] = src2[i];
-    }
-    __syncthreads();
+struct Tally {
+    unsigned att[4], acc[4], rej_geom, rej_bond, rechecks;
+    unsigned long long pairs;
+    double dE_cell;
+};
 
+// copy the model tables and move mix into the block's shared memory
+__device__ __forceinline__ void load_tables(const DevState &d, ModelDev &md, MixDev &mx)
+{
+    const int *src = (const int *)d.model;
+    int *dst = (int *)&md;
+    for (int i = threadIdx.x; i < (int)(sizeof(ModelDev) / 4); i += blockDim.x) dst[i] = src[i];
+    const int *src2 = (const int *)d.mix;
+    int *dst2 = (int *)&mx;
+    for (int i = threadIdx.x; i < (int)(sizeof(MixDev) / 4); i += blockDim.x) dst2[i] = src2[i];
+}
+
+// All n attempts of active cell g of the colour, by the 32 W threads of one
+// group (group index gid within the block, its shared memory at gsmem).
+template <int PREC, int W>
+__device__ void run_cell(const DevState &d, int buf, int colour, const LogArgs &lg, int g, const ModelDev &md,
+                         const MixDev &mx, unsigned char *gsmem, int gid)
+{
+    constexpr int T = 32 * W;          // threads per cell
+    const int gt = threadIdx.x % T;
     const int lane = threadIdx.x & 31;
-    const int wib = threadIdx.x >> 5;
-    const int g = blockIdx.x * (blockDim.x >> 5) + wib;
-    if (g >= d.n_act) return;
+    const int wig = gt >> 5;
     const int cap = d.stencil_cap;
-    const Scratch ws = carve(smem + (size_t)wib * scratch_bytes(cap), cap);
+    const int rec_cap = d.full_rec ? cap : d.own_cap;
+    const Group G = carve(gsmem, cap, rec_cap, W);
+    const WarpScr S = warp_scr(G, wig);
 
     // ---- which cell ----
     const int r = find_segment(d.act_off, d.n_rep, g);
@@ -449,340 +999,283 @@ __global__ void __launch_bounds__(128) phase_kernel(DevState d, int buf, int col
     const bool small = nc == 2;
     const int ns = small ? 8 : 27;
 
-    // ---- stage the neighbourhood: own cell first ----
-    int cnt = 0, cst = 0;
-    if (lane < ns) {
-        int ox, oy, oz;
-        if (small) {
-            ox = lane & 1; oy = (lane >> 1) & 1; oz = lane >> 2;
-        } else {
-            const int k = (lane == 0) ? 13 : (lane <= 13 ? lane - 1 : lane);   // 13 = (0,0,0)
-            ox = k % 3 - 1; oy = (k / 3) % 3 - 1; oz = k / 9 - 1;
+    // ---- neighbourhood: own cell first ----
+    if (wig == 0) {
+        int cnt = 0, cst = 0;
+        if (lane < ns) {
+            int ox, oy, oz;
+            if (small) {
+                ox = lane & 1; oy = (lane >> 1) & 1; oz = lane >> 2;
+            } else {
+                const int kk = (lane == 0) ? 13 : (lane <= 13 ? lane - 1 : lane);   // 13 = (0,0,0)
+                ox = kk % 3 - 1; oy = (kk / 3) % 3 - 1; oz = kk / 9 - 1;
+            }
+            const int nx = (cx + ox + nc) % nc, ny = (cy + oy + nc) % nc, nz = (cz + oz + nc) % nc;
+            const int c = ri.cell_off + (nz * nc + ny) * nc + nx;
+            cst = d.cell_start[c];
+            cnt = d.cell_start[c + 1] - cst;
         }
-        const int nx = (cx + ox + nc) % nc, ny = (cy + oy + nc) % nc, nz = (cz + oz + nc) % nc;
-        const int c = ri.cell_off + (nz * nc + ny) * nc + nx;
-        cst = d.cell_start[c];
-        cnt = d.cell_start[c + 1] - cst;
-    }
-    int incl = cnt;
+        int incl = cnt;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(FULL, incl, o);
-        if (lane >= o) incl += y;
-    }
-    const int K = __shfl_sync(FULL, incl, 31);
-    const int n = __shfl_sync(FULL, cnt, 0);
-    const int own_start = __shfl_sync(FULL, cst, 0);
-    if (K > cap) {
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane < ns) {
+            G.cstart[lane] = cst;
+            G.coff[lane] = incl - cnt;
+        }
+        if (lane == 31) {
+            G.coff[ns] = incl;
+            G.misc[MS_K] = incl;
+        }
         if (lane == 0) {
+            G.misc[MS_N] = cnt;
+            G.misc[MS_START] = cst;
+        }
+    }
+    gsync<W>(gid);
+    const int K = G.misc[MS_K];
+    const int n = G.misc[MS_N];
+    const int own_start = G.misc[MS_START];
+    if (K + 1 > cap || n > rec_cap) {
+        if (gt == 0) {
             atomicOr(d.err, ERR_STENCIL);
             d.cell_dE[cellG] = 0.0;
         }
         return;
     }
-    if (lane < ns) {
-        ws.cstart[lane] = cst;
-        ws.coff[lane] = incl - cnt;
-    }
-    if (lane == 0) ws.coff[ns] = K;
-    __syncwarp();
 
-    // cell-local frame for FP32 coordinates: the cell centre
-    const uint32_t P[3] = {
-        (uint32_t)(((uint64_t)(2 * cx + 1) << 32) / (uint64_t)(2 * nc)) - ct.shift[0],
-        (uint32_t)(((uint64_t)(2 * cy + 1) << 32) / (uint64_t)(2 * nc)) - ct.shift[1],
-        (uint32_t)(((uint64_t)(2 * cz + 1) << 32) / (uint64_t)(2 * nc)) - ct.shift[2]};
-    const float hf = ri.hf;
-    auto local = [&](uint32_t x, uint32_t y, uint32_t z) {
-        PosF p;
-        p.x = (float)(int)(x - P[0]) * hf;
-        p.y = (float)(int)(y - P[1]) * hf;
-        p.z = (float)(int)(z - P[2]) * hf;
-        return p;
-    };
-    const int4 *src = d.rec[buf];
-    for (int idx = lane; idx < K; idx += 32) {
-        const int k = find_segment(ws.coff, ns, idx);
-        const int4 rc = src[ws.cstart[k] + (idx - ws.coff[k])];
-        ws.rec[idx] = rc;
-        if (PREC == MC_PREC_FP32 && !small) {
-            const PosF p = local((uint32_t)rc.x, (uint32_t)rc.y, (uint32_t)rc.z);
-            ws.pos[idx] = make_float4(p.x, p.y, p.z, __int_as_float(rc.w));
+    CellCtx c;
+    c.md = &md;
+    c.mx = &mx;
+    c.K = K;
+    c.n = n;
+    c.cellL = cellL;
+    c.nc = nc;
+    c.small = small;
+    c.shift[0] = ct.shift[0];
+    c.shift[1] = ct.shift[1];
+    c.shift[2] = ct.shift[2];
+    c.P[0] = (uint32_t)(((uint64_t)(2 * cx + 1) << 32) / (uint64_t)(2 * nc)) - ct.shift[0];
+    c.P[1] = (uint32_t)(((uint64_t)(2 * cy + 1) << 32) / (uint64_t)(2 * nc)) - ct.shift[1];
+    c.P[2] = (uint32_t)(((uint64_t)(2 * cz + 1) << 32) / (uint64_t)(2 * nc)) - ct.shift[2];
+    c.sweep = ct.sweep;
+    c.seed = dy.seed;
+    c.h = ri.h;
+    c.inv_h = ri.inv_h;
+    c.hf = ri.hf;
+    c.T64 = dy.T;
+    c.T32 = (float)dy.T;
+    c.D_atom = dy.D_atom;
+    c.D_mol = dy.D_mol;
+    c.gap = md.recheck_gap_f;
+    c.err = d.err;
+    float rc2max = 0.f;
+    for (int kk = 0; kk < 9; ++kk) rc2max = fmaxf(rc2max, md.rc2f[kk]);
+    c.rc2max = rc2max;
+    c.pre_r2 = rc2max * 1.01f;
+    c.rv.smem = G.rec;
+    c.rv.full = d.full_rec != 0;
+    c.rv.n = n;
+    c.rv.gsrc = d.rec[buf];
+    c.rv.cstart = G.cstart;
+    c.rv.coff = G.coff;
+    c.rv.ns = ns;
+    const float rconf2 = rc2max * 1.0201f;   // (1.01 rc)^2
+
+    // ---- stage: issue all loads of a thread before using any ----
+    {
+        const int4 *src = d.rec[buf];
+        constexpr int UNR = 4;
+        int kk = 0;   // neighbour cell of the current index (indices only grow)
+        for (int base = gt; base < K; base += UNR * T) {
+            int4 rc[UNR];
+#pragma unroll
+            for (int u = 0; u < UNR; ++u) {
+                const int idx = base + u * T;
+                if (idx < K) {
+                    while (G.coff[kk + 1] <= idx) ++kk;
+                    rc[u] = src[G.cstart[kk] + (idx - G.coff[kk])];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < UNR; ++u) {
+                const int idx = base + u * T;
+                if (idx < K) {
+                    if (idx < rec_cap) G.rec[idx] = rc[u];
+                    G.sw[idx] = rc[u].w;
+                    const PosF p = local_of(c, (uint32_t)rc[u].x, (uint32_t)rc[u].y, (uint32_t)rc[u].z);
+                    G.sx[idx] = p.x;
+                    G.sy[idx] = p.y;
+                    G.sz[idx] = p.z;
+                }
+            }
+        }
+        if (gt == 0) {
+            // padding partner for the odd last pair: far away, no molecule
+            G.sx[K] = FAR;
+            G.sy[K] = FAR;
+            G.sz[K] = FAR;
+            G.sw[K] = 0x7FFFFFFF;
+            if (K < rec_cap) G.rec[K] = make_int4(0, 0, 0, 0x7FFFFFFF);
         }
     }
-    __syncwarp();
+    gsync<W>(gid);
 
-    float rc2max = 0.f;
-    for (int k = 0; k < 9; ++k) rc2max = fmaxf(rc2max, md.rc2f[k]);
-    const float pre_r2 = rc2max * 1.01f;
-    const double T = dy.T;
-    const double gap = (double)md.recheck_gap_f;
-
-    unsigned att[4] = {0, 0, 0, 0}, acc[4] = {0, 0, 0, 0};
-    unsigned rej_geom = 0, rej_bond = 0, rechecks = 0;
-    unsigned long long pairs = 0;
-    double dE_cell = 0.0;
-
+    Tally t{};
     for (int a0 = 0; a0 < n; a0 += 32) {
-        // random numbers and thresholds of attempts a0 .. a0+31
-        {
+        if (wig == 0) {
+            // random words and thresholds drawn by the cell-list build, one slot per attempt
             const int a = a0 + lane;
             if (a < n) {
-                const U4 b0 = rng_block((uint32_t)(2 * a), (uint32_t)cellL, ct.sweep, dy.seed);
-                const U4 b1 = rng_block((uint32_t)(2 * a + 1), (uint32_t)cellL, ct.sweep, dy.seed);
-                uint32_t *w = ws.rnd + 8 * lane;
-                w[0] = b0.x; w[1] = b0.y; w[2] = b0.z; w[3] = b0.w;
-                w[4] = b1.x; w[5] = b1.y; w[6] = b1.z; w[7] = b1.w;
-                const unsigned long long u52 = ((unsigned long long)b0.z << 20) | (unsigned long long)(b0.w >> 12);
-                const double u = __dmul_rn((double)(2ull * u52 + 1ull), 0x1p-53);
-                ws.thr[lane] = -__dmul_rn(T, ln_series(u));
+                const size_t slot = (size_t)own_start + (size_t)a;
+                const uint4 b0 = d.att_rnd[2 * slot], b1 = d.att_rnd[2 * slot + 1];
+                uint4 *w = (uint4 *)(G.rnd + 8 * lane);
+                w[0] = b0;
+                w[1] = b1;
+                if (PREC == MC_PREC_FP64) G.thr64[lane] = d.att_thr64[slot];
+                else G.thr32[lane] = d.att_thr32[slot];
             }
         }
-        __syncwarp();
+        gsync<W>(gid);
         const int a_end = min(n, a0 + 32);
-        for (int a = a0; a < a_end; ++a) {
-            const uint32_t *w = ws.rnd + 8 * (a - a0);
-            const double thr = ws.thr[a - a0];
-            const int k = (int)(((unsigned long long)w[0] * (unsigned long long)n) >> 32);
-            const int4 ri_rec = ws.rec[k];
-            const int wi = ri_rec.w;
-            const int mol = rec_mol(wi);
-            const int mvt = move_type(w[1], mx);
-            int status = MC_ST_EVALUATED;
-            double dE = 0.0, dE64 = __longlong_as_double(0x7FF8000000000000ll);
-            float scale = 0.f;
-            int flags = 0;
-            Move mv;
-            mv.mol = mol;
-            mv.intra = false;
-            int kslot[3] = {k, -1, -1};
-            att[mvt] += 1;
-
-            if (mvt == MC_MOVE_ATOM) {
-                mv.n = 1;
-                mv.site[0] = rec_site(wi);
-                mv.qo[0][0] = (uint32_t)ri_rec.x; mv.qo[0][1] = (uint32_t)ri_rec.y; mv.qo[0][2] = (uint32_t)ri_rec.z;
-                for (int ax = 0; ax < 3; ++ax) mv.qn[0][ax] = mv.qo[0][ax] + (uint32_t)uniform_disp(w[4 + ax], dy.D_atom);
-                mv.to[0] = mv.tn[0] = rec_type(wi);
-                mv.moves_pos = true;
-                if (cell_local(mv.qn[0][0], mv.qn[0][1], mv.qn[0][2], ct.shift, nc) != cellL) status = MC_ST_LEFT_CELL;
-            } else if (mvt == MC_MOVE_FLIP) {
-                const int axis = (int)(((unsigned long long)w[7] * 3ull) >> 32);
-                const int sp = axis == 0 ? 1 : 0, sq = axis == 2 ? 1 : 2;
-                int kp = -1, kq = -1;
-                for (int j = lane; j < n; j += 32) {
-                    const int wj = ws.rec[j].w;
-                    if (rec_mol(wj) == mol) {
-                        if (rec_slot(wj) == sp) kp = j;
-                        if (rec_slot(wj) == sq) kq = j;
+        int a = a0;
+        while (a < a_end) {
+            // evaluate attempts a .. a+W-1, one per warp, on the same state
+            if (a + wig < a_end) evaluate<PREC, W>(c, G, S, G.res + wig, a + wig - a0, lane);
+            gsync<W>(gid);
+            if (gt == 0) {
+                // commit in order, up to the first attempt an earlier accepted one may have changed
+                const int nw = min(W, a_end - a);
+                int adv = 0;
+                for (int wj = 0; wj < nw; ++wj) {
+                    const Res &R = G.res[wj];
+                    if (W > 1) {
+                        bool clash = false;
+                        for (int wa = 0; wa < wj && !clash; ++wa)
+                            if (G.res[wa].accept) clash = conflicts(G.res[wa], R, rconf2);
+                        if (clash) break;
                     }
+                    const int at = a + wj;
+                    t.att[R.mvt] += 1;
+                    if (R.status == MC_ST_LEFT_CELL || R.status == MC_ST_NOT_IN_CELL) t.rej_geom += 1;
+                    if (R.status == MC_ST_BOND_BREAK) t.rej_bond += 1;
+                    if (R.status == MC_ST_EVALUATED || R.status == MC_ST_BOND_BREAK)
+                        t.pairs += (unsigned long long)R.pairs * (unsigned long long)K;
+                    t.rechecks += R.flags;
+                    if (R.accept) {
+                        t.acc[R.mvt] += 1;
+                        t.dE_cell = __dadd_rn(t.dE_cell, R.dE_used);
+                        if (R.mvt == MC_MOVE_FLIP) {
+                            for (int s = 0; s < 2; ++s) {
+                                int4 rs = G.rec[R.ks[s]];
+                                rs.w = (rs.w & ~3) | R.t3n[s];
+                                G.rec[R.ks[s]] = rs;
+                                G.sw[R.ks[s]] = rs.w;
+                            }
+                        } else {
+                            for (int s = 0; s < R.nmv; ++s) {
+                                int4 rs = G.rec[R.ks[s]];
+                                rs.x = (int)R.qn[s][0];
+                                rs.y = (int)R.qn[s][1];
+                                rs.z = (int)R.qn[s][2];
+                                G.rec[R.ks[s]] = rs;
+                                const PosF p = local_of(c, R.qn[s][0], R.qn[s][1], R.qn[s][2]);
+                                G.sx[R.ks[s]] = p.x;
+                                G.sy[R.ks[s]] = p.y;
+                                G.sz[R.ks[s]] = p.z;
+                            }
+                        }
+                    }
+                    if (lg.base != nullptr) {
+                        const uint64_t sl = ct.sweep - lg.sweep0;
+                        mc_log_entry *e = lg.base + (size_t)ri.site_off * (size_t)lg.n_sweeps +
+                                          (size_t)sl * (size_t)ri.n_sites + (size_t)(own_start - ri.site_off) +
+                                          (size_t)at;
+                        e->site = R.site;
+                        e->move = (int16_t)R.mvt;
+                        e->flags = (int16_t)R.flags;
+                        e->status = R.status;
+                        e->accepted = R.accept;
+                        e->dE = R.status == MC_ST_EVALUATED ? R.dE_log : __longlong_as_double(0x7FF8000000000000ll);
+                        e->dE64 = R.dE64;
+                        e->scale = (double)R.scale;
+                    }
+                    ++adv;
                 }
-                kp = __reduce_max_sync(FULL, kp);
-                kq = __reduce_max_sync(FULL, kq);
-                if (kp < 0 || kq < 0) {
-                    status = MC_ST_NOT_IN_CELL;
-                } else {
-                    kslot[0] = kp; kslot[1] = kq;
-                    const int4 rp = ws.rec[kp], rq = ws.rec[kq];
-                    mv.n = 2;
-                    mv.site[0] = rec_site(rp.w); mv.site[1] = rec_site(rq.w);
-                    mv.qo[0][0] = mv.qn[0][0] = (uint32_t)rp.x; mv.qo[0][1] = mv.qn[0][1] = (uint32_t)rp.y;
-                    mv.qo[0][2] = mv.qn[0][2] = (uint32_t)rp.z;
-                    mv.qo[1][0] = mv.qn[1][0] = (uint32_t)rq.x; mv.qo[1][1] = mv.qn[1][1] = (uint32_t)rq.y;
-                    mv.qo[1][2] = mv.qn[1][2] = (uint32_t)rq.z;
-                    mv.to[0] = rec_type(rp.w); mv.to[1] = rec_type(rq.w);
-                    mv.tn[0] = mv.to[1]; mv.tn[1] = mv.to[0];
-                    mv.moves_pos = false;
-                }
+                if (W > 1) G.misc[MS_ADV] = adv;
+            }
+            if constexpr (W == 1) {
+                __syncwarp();
+                a += 1;
             } else {
-                int ks[3] = {-1, -1, -1};
-                for (int j = lane; j < n; j += 32) {
-                    const int wj = ws.rec[j].w;
-                    if (rec_mol(wj) == mol) ks[rec_slot(wj)] = j;
-                }
-                for (int s = 0; s < 3; ++s) ks[s] = __reduce_max_sync(FULL, ks[s]);
-                if (ks[0] < 0 || ks[1] < 0 || ks[2] < 0) {
-                    status = MC_ST_NOT_IN_CELL;
-                } else {
-                    mv.n = 3;
-                    mv.moves_pos = true;
-                    for (int s = 0; s < 3; ++s) {
-                        kslot[s] = ks[s];
-                        const int4 rs = ws.rec[ks[s]];
-                        mv.site[s] = rec_site(rs.w);
-                        mv.qo[s][0] = (uint32_t)rs.x; mv.qo[s][1] = (uint32_t)rs.y; mv.qo[s][2] = (uint32_t)rs.z;
-                        mv.to[s] = mv.tn[s] = rec_type(rs.w);
-                    }
-                    if (mvt == MC_MOVE_MOL_TRANS) {
-                        int32_t dd[3];
-                        for (int ax = 0; ax < 3; ++ax) dd[ax] = uniform_disp(w[4 + ax], dy.D_mol);
-                        for (int s = 0; s < 3; ++s)
-                            for (int ax = 0; ax < 3; ++ax) mv.qn[s][ax] = mv.qo[s][ax] + (uint32_t)dd[ax];
-                    } else {
-                        rotate_molecule(mv.qo, mv.qn, w + 4, mx.rot_a, ri.h, ri.inv_h);
-                        mv.intra = true;
-                    }
-                    for (int s = 0; s < 3; ++s)
-                        if (cell_local(mv.qn[s][0], mv.qn[s][1], mv.qn[s][2], ct.shift, nc) != cellL)
-                            status = MC_ST_LEFT_CELL;
-                }
+                gsync<W>(gid);
+                a += G.misc[MS_ADV];
+                gsync<W>(gid);
             }
-
-            bool accept = false;
-            if (status == MC_ST_EVALUATED) {
-                if (PREC == MC_PREC_FP64) {
-                    status = dE64_ordered(mv, ws, K, md, ri.h, hf, pre_r2, lane, d.err, dE);
-                    dE64 = dE;
-                    accept = status == MC_ST_EVALUATED && dE <= thr;
-                    pairs += (unsigned long long)(2 * mv.n) * (unsigned long long)K;
-                } else {
-                    Acc32 acc32;
-                    if (mvt == MC_MOVE_ATOM) {
-                        const PosF so = local(mv.qo[0][0], mv.qo[0][1], mv.qo[0][2]);
-                        const PosF sn = local(mv.qn[0][0], mv.qn[0][1], mv.qn[0][2]);
-                        acc32 = small ? atom_dE32<true>(ws, K, md, wi, mv.to[0], so, sn, mv.qo[0], mv.qn[0], hf, rc2max, lane)
-                                      : atom_dE32<false>(ws, K, md, wi, mv.to[0], so, sn, mv.qo[0], mv.qn[0], hf, rc2max, lane);
-                        pairs += 2ull * (unsigned long long)K;
-                    } else if (mvt == MC_MOVE_FLIP) {
-                        const PosF sp = local(mv.qo[0][0], mv.qo[0][1], mv.qo[0][2]);
-                        const PosF sq = local(mv.qo[1][0], mv.qo[1][1], mv.qo[1][2]);
-                        const int wp2 = (int)((uint32_t)ws.rec[kslot[0]].w >> 2);
-                        const int wq2 = (int)((uint32_t)ws.rec[kslot[1]].w >> 2);
-                        acc32 = small ? flip_dE32<true>(ws, K, md, mol, wp2, wq2, mv.to[0], mv.to[1], sp, sq, mv.qo[0], mv.qo[1], hf, rc2max, lane)
-                                      : flip_dE32<false>(ws, K, md, mol, wp2, wq2, mv.to[0], mv.to[1], sp, sq, mv.qo[0], mv.qo[1], hf, rc2max, lane);
-                        pairs += 2ull * (unsigned long long)K;
-                    } else {
-                        PosF so[3], sn[3];
-                        for (int s = 0; s < 3; ++s) {
-                            so[s] = local(mv.qo[s][0], mv.qo[s][1], mv.qo[s][2]);
-                            sn[s] = local(mv.qn[s][0], mv.qn[s][1], mv.qn[s][2]);
-                        }
-                        acc32 = small ? mol_dE32<true>(ws, K, md, mol, mv.to, so, sn, mv.qo, mv.qn, hf, rc2max, lane)
-                                      : mol_dE32<false>(ws, K, md, mol, mv.to, so, sn, mv.qo, mv.qn, hf, rc2max, lane);
-                        pairs += 6ull * (unsigned long long)K;
-                        if (mv.intra) {
-                            // intramolecular bonds change under rotation: add them (uniform on all lanes)
-                            const int pk[3] = {0, 0, 1}, pl[3] = {1, 2, 2};
-                            for (int pr = 0; pr < 3; ++pr) {
-                                const int kk = pk[pr], ll = pl[pr];
-                                const int ab = 3 * mv.to[kk] + mv.to[ll];
-                                const float r2o = r2_int32f(mv.qo[ll][0], mv.qo[ll][1], mv.qo[ll][2], mv.qo[kk], hf);
-                                const float r2n = r2_int32f(mv.qn[ll][0], mv.qn[ll][1], mv.qn[ll][2], mv.qn[kk], hf);
-                                if (r2n * md.invR2f[ab] >= md.bond_guard_f || r2o * md.invR2f[ab] >= md.bond_guard_f) {
-                                    acc32.guard = 1;
-                                    continue;
-                                }
-                                float u, m;
-                                if (r2o < md.rc2f[ab]) { wca32(md, r2o, ab, u, m); acc32.dE -= u; acc32.mag += m; }
-                                if (r2n < md.rc2f[ab]) { wca32(md, r2n, ab, u, m); acc32.dE += u; acc32.mag += m; }
-                                fene32(md, r2o, ab, u, m); acc32.dE -= u; acc32.mag += m;
-                                fene32(md, r2n, ab, u, m); acc32.dE += u; acc32.mag += m;
-                            }
-                        }
-                    }
-                    dE = (double)acc32.dE;
-                    scale = acc32.mag;
-                    const double diff = fabs(dE - thr);
-                    if (acc32.guard || !(diff > gap * (double)acc32.mag)) {
-                        flags = 1;
-                        rechecks += 1;
-                        status = dE64_ordered(mv, ws, K, md, ri.h, hf, pre_r2, lane, d.err, dE64);
-                        accept = status == MC_ST_EVALUATED && dE64 <= thr;
-                    } else {
-                        accept = dE <= thr;
-                    }
-                }
-            }
-
-            if (status == MC_ST_LEFT_CELL || status == MC_ST_NOT_IN_CELL) rej_geom += 1;
-            if (status == MC_ST_BOND_BREAK) rej_bond += 1;
-            if (accept) {
-                acc[mvt] += 1;
-                const double used = (PREC == MC_PREC_FP64 || flags) ? dE64 : dE;
-                dE_cell = __dadd_rn(dE_cell, used);
-                if (lane == 0) {
-                    if (mvt == MC_MOVE_FLIP) {
-                        int4 rp = ws.rec[kslot[0]], rq = ws.rec[kslot[1]];
-                        rp.w = (rp.w & ~3) | mv.tn[0];
-                        rq.w = (rq.w & ~3) | mv.tn[1];
-                        ws.rec[kslot[0]] = rp;
-                        ws.rec[kslot[1]] = rq;
-                        if (PREC == MC_PREC_FP32 && !small) {
-                            ws.pos[kslot[0]].w = __int_as_float(rp.w);
-                            ws.pos[kslot[1]].w = __int_as_float(rq.w);
-                        }
-                    } else {
-                        for (int s = 0; s < mv.n; ++s) {
-                            int4 rs = ws.rec[kslot[s]];
-                            rs.x = (int)mv.qn[s][0]; rs.y = (int)mv.qn[s][1]; rs.z = (int)mv.qn[s][2];
-                            ws.rec[kslot[s]] = rs;
-                            if (PREC == MC_PREC_FP32 && !small) {
-                                const PosF p = local(mv.qn[s][0], mv.qn[s][1], mv.qn[s][2]);
-                                ws.pos[kslot[s]] = make_float4(p.x, p.y, p.z, __int_as_float(rs.w));
-                            }
-                        }
-                    }
-                }
-            }
-            if (lg.base != nullptr && lane == 0) {
-                const uint64_t sl = ct.sweep - lg.sweep0;
-                mc_log_entry *e = lg.base + (size_t)ri.site_off * (size_t)lg.n_sweeps + (size_t)sl * (size_t)ri.n_sites +
-                                  (size_t)(own_start - ri.site_off) + (size_t)a;
-                e->site = rec_site(wi);
-                e->move = (int16_t)mvt;
-                e->flags = (int16_t)flags;
-                e->status = status;
-                e->accepted = accept ? 1 : 0;
-                e->dE = status == MC_ST_EVALUATED ? dE : __longlong_as_double(0x7FF8000000000000ll);
-                e->dE64 = dE64;
-                e->scale = (double)scale;
-            }
-            __syncwarp();
         }
     }
 
     // ---- write back the cell; count periodic images crossed ----
     int4 *dst = d.rec[buf] + own_start;
-    for (int k = lane; k < n; k += 32) {
-        const int4 nw = ws.rec[k];
-        const int4 od = dst[k];
+    for (int kk = gt; kk < n; kk += T) {
+        const int4 nw = G.rec[kk];
+        const int4 od = dst[kk];
         const int site = ri.site_off + rec_site(nw.w);
         const uint32_t o3[3] = {(uint32_t)od.x, (uint32_t)od.y, (uint32_t)od.z};
         const uint32_t n3[3] = {(uint32_t)nw.x, (uint32_t)nw.y, (uint32_t)nw.z};
+#pragma unroll
         for (int ax = 0; ax < 3; ++ax) {
             const long long moved = (long long)o3[ax] + (long long)(int)(n3[ax] - o3[ax]);
             if (moved < 0) d.img[3 * site + ax] -= 1;
             else if (moved >= 4294967296ll) d.img[3 * site + ax] += 1;
         }
-        dst[k] = nw;
+        dst[kk] = nw;
     }
-    if (lane == 0) {
-        d.cell_dE[cellG] = dE_cell;
+    if (gt == 0) {
+        d.cell_dE[cellG] = t.dE_cell;
         unsigned long long *st = d.stats + (size_t)r * STAT_N;
         for (int m = 0; m < 4; ++m) {
-            if (att[m]) atomicAdd(st + STAT_ATT + m, (unsigned long long)att[m]);
-            if (acc[m]) atomicAdd(st + STAT_ACC + m, (unsigned long long)acc[m]);
+            if (t.att[m]) atomicAdd(st + STAT_ATT + m, (unsigned long long)t.att[m]);
+            if (t.acc[m]) atomicAdd(st + STAT_ACC + m, (unsigned long long)t.acc[m]);
         }
-        if (rej_geom) atomicAdd(st + STAT_REJ_GEOM, (unsigned long long)rej_geom);
-        if (rej_bond) atomicAdd(st + STAT_REJ_BOND, (unsigned long long)rej_bond);
-        if (pairs) atomicAdd(st + STAT_PAIRS, pairs);
-        if (rechecks) atomicAdd(st + STAT_RECHECK, (unsigned long long)rechecks);
+        if (t.rej_geom) atomicAdd(st + STAT_REJ_GEOM, (unsigned long long)t.rej_geom);
+        if (t.rej_bond) atomicAdd(st + STAT_REJ_BOND, (unsigned long long)t.rej_bond);
+        if (t.pairs) atomicAdd(st + STAT_PAIRS, t.pairs);
+        if (t.rechecks) atomicAdd(st + STAT_RECHECK, (unsigned long long)t.rechecks);
     }
 }
 
-// Per replica: add the sweep's accepted Delta E (cells in a fixed reduction
-// order, so the result is reproducible), count the sweep, advance the counter.
-__global__ void __launch_bounds__(256) finalize_kernel(DevState d)
+// One colour phase, one launch: group g of the grid owns active cell g.
+template <int PREC, int W>
+__global__ void __launch_bounds__(BLOCK) phase_kernel(DevState d, int buf, int colour, LogArgs lg)
 {
-    const int r = blockIdx.x;
+    constexpr int CPB = BLOCK / (32 * W);
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ ModelDev md;
+    __shared__ MixDev mx;
+    load_tables(d, md, mx);
+    __syncthreads();
+    const int gid = threadIdx.x / (32 * W);
+    const int g = blockIdx.x * CPB + gid;
+    if (g >= d.n_act) return;          // whole group leaves together
+    const int rec_cap = d.full_rec ? d.stencil_cap : d.own_cap;
+    run_cell<PREC, W>(d, buf, colour, lg, g, md, mx, smem + (size_t)gid * group_bytes(d.stencil_cap, rec_cap, W), gid);
+}
+
+// Per replica (one block of BLOCK threads): add the sweep's accepted Delta E,
+// the cells summed in a fixed partition and reduction tree so the result is
+// reproducible; count the sweep; advance the sweep counter.
+__device__ void finalize_replica(const DevState &d, int r, double *red)
+{
     const RepInfo ri = d.rep[r];
     const int ncell = ri.nc * ri.nc * ri.nc;
     double s = 0.0;
-    for (int c = threadIdx.x; c < ncell; c += 256) s = __dadd_rn(s, d.cell_dE[ri.cell_off + c]);
-    __shared__ double red[256];
+    for (int c = threadIdx.x; c < ncell; c += BLOCK) s = __dadd_rn(s, d.cell_dE[ri.cell_off + c]);
     red[threadIdx.x] = s;
     __syncthreads();
-    for (int w = 128; w > 0; w >>= 1) {
+    for (int w = BLOCK / 2; w > 0; w >>= 1) {
         if (threadIdx.x < w) red[threadIdx.x] = __dadd_rn(red[threadIdx.x], red[threadIdx.x + w]);
         __syncthreads();
     }
@@ -791,45 +1284,271 @@ __global__ void __launch_bounds__(256) finalize_kernel(DevState d)
         d.stats[(size_t)r * STAT_N + STAT_SWEEPS] += 1;
         d.ctr[r].sweep += 1;
     }
+    __syncthreads();
 }
 
-size_t phase_smem_bytes(int stencil_cap, int warps_per_block)
+__global__ void __launch_bounds__(BLOCK) finalize_kernel(DevState d)
 {
-    return scratch_bytes(stencil_cap) * (size_t)warps_per_block;
+    __shared__ double red[BLOCK];
+    finalize_replica(d, blockIdx.x, red);
 }
 
-int phase_set_smem_limit(int stencil_cap, int warps_per_block)
+// ---------------------------------------------------------------------------
+// Persistent sweeps: one cooperative launch runs n_sweeps whole sweeps (cell
+// list, 8 colour phases, finalisation), the stages separated by a grid-wide
+// barrier.  Every wait of the barrier is bounded: after about a second it
+// records ERR_TIMEOUT and the kernel leaves, instead of waiting forever.
+// ---------------------------------------------------------------------------
+struct GridBar {
+    unsigned int *count;
+    unsigned int *gen;
+    int *scan_tot;       // one per block: cell-count total of the block's chunk
+};
+
+__device__ bool grid_sync(const GridBar &gb, int *err)
+{
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ok = 1;
+        volatile unsigned int *vgen = gb.gen;
+        const unsigned int g0 = *vgen;
+        __threadfence();
+        const unsigned int arrived = atomicAdd(gb.count, 1u);
+        if (arrived == gridDim.x - 1) {
+            atomicExch(gb.count, 0u);
+            __threadfence();
+            atomicAdd(gb.gen, 1u);
+        } else {
+            unsigned long long spins = 0;
+            while (*vgen == g0) {
+                if (++spins > (1ull << 24)) {
+                    atomicOr(err, ERR_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// exclusive prefix sum over a block of BLOCK threads (one value per thread)
+__device__ __forceinline__ int block_excl_scan(int v, int *tmp, int &total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(FULL, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) tmp[warp] = x;
+    __syncthreads();
+    int before = 0;
+    total = 0;
+    for (int w = 0; w < BLOCK / 32; ++w) {
+        if (w < warp) before += tmp[w];
+        total += tmp[w];
+    }
+    __syncthreads();
+    return before + x - v;
+}
+
+template <int PREC, int W>
+__global__ void __launch_bounds__(BLOCK) sweep_persistent(DevState d, int buf0, int n_sweeps, GridBar gb)
+{
+    constexpr int T = 32 * W;
+    constexpr int CPB = BLOCK / T;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ ModelDev md;
+    __shared__ MixDev mx;
+    __shared__ double red[BLOCK];
+    __shared__ int tmp[BLOCK / 32];
+    load_tables(d, md, mx);
+    __syncthreads();
+    const int nthr = gridDim.x * BLOCK;
+    const int tid = blockIdx.x * BLOCK + threadIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int gid = threadIdx.x / T;
+    const int rec_cap = d.full_rec ? d.stencil_cap : d.own_cap;
+    unsigned char *gsmem = smem + (size_t)gid * group_bytes(d.stencil_cap, rec_cap, W);
+    const LogArgs none{nullptr, 0, 0};
+    const int nC = d.n_cells;
+    const int chunk = (nC + gridDim.x - 1) / gridDim.x;
+    const int lo = min(nC, (int)blockIdx.x * chunk), hi = min(nC, lo + chunk);
+    int buf = buf0;
+    for (int s = 0; s < n_sweeps; ++s) {
+        // ---- cell list: count (cell_count is zero on entry) ----
+        for (int g = tid; g < d.n_sites; g += nthr) cl_count_item(d, buf, g);
+        if (!grid_sync(gb, d.err)) return;
+        // ---- exclusive scan: chunk totals, then each block scans its chunk ----
+        {
+            int sum = 0;
+            for (int c = lo + threadIdx.x; c < hi; c += BLOCK) sum += d.cell_count[c];
+            int total;
+            block_excl_scan(sum, tmp, total);
+            if (threadIdx.x == 0) gb.scan_tot[blockIdx.x] = total;
+        }
+        if (!grid_sync(gb, d.err)) return;
+        {
+            int off = 0, all = 0;
+            for (int b = threadIdx.x; b < (int)gridDim.x; b += BLOCK) {
+                const int v = gb.scan_tot[b];
+                all += v;
+                if (b < (int)blockIdx.x) off += v;
+            }
+            int t1, t2;
+            block_excl_scan(off, tmp, t1);
+            block_excl_scan(all, tmp, t2);
+            int carry = t1;                       // sum of the totals of earlier blocks
+            for (int base = lo; base < hi; base += BLOCK) {
+                const int c = base + threadIdx.x;
+                const int v = c < hi ? d.cell_count[c] : 0;
+                int tile;
+                const int ex = block_excl_scan(v, tmp, tile);
+                if (c < hi) d.cell_start[c] = carry + ex;
+                carry += tile;
+            }
+            if (blockIdx.x == 0 && threadIdx.x == 0) d.cell_start[nC] = t2;
+        }
+        if (!grid_sync(gb, d.err)) return;
+        // ---- scatter, then order each cell and draw its attempts' random numbers ----
+        for (int g = tid; g < d.n_sites; g += nthr) cl_scatter_item(d, buf, buf ^ 1, g);
+        if (!grid_sync(gb, d.err)) return;
+        for (int c = blockIdx.x * (BLOCK / 32) + warp; c < nC; c += gridDim.x * (BLOCK / 32))
+            cl_order_cell(d, buf ^ 1, c, lane);
+        if (!grid_sync(gb, d.err)) return;
+        // ---- the 8 colours ----
+        for (int colour = 0; colour < 8; ++colour) {
+            for (int g = blockIdx.x * CPB + gid; g < d.n_act; g += gridDim.x * CPB)
+                run_cell<PREC, W>(d, buf ^ 1, colour, none, g, md, mx, gsmem, gid);
+            if (!grid_sync(gb, d.err)) return;
+        }
+        // ---- finalise the sweep; clear the counts for the next one ----
+        for (int r = blockIdx.x; r < d.n_rep; r += gridDim.x) finalize_replica(d, r, red);
+        for (int c = tid; c < nC; c += nthr) d.cell_count[c] = 0;
+        if (!grid_sync(gb, d.err)) return;
+        buf ^= 1;
+    }
+}
+
+size_t phase_smem_bytes(int stencil_cap, int rec_cap, int warps_per_cell)
+{
+    return group_bytes(stencil_cap, rec_cap, warps_per_cell) * (size_t)(BLOCK / (32 * warps_per_cell));
+}
+
+template <class K>
+static bool set_kernel_smem(K kernel, int bytes)
+{
+    // one shared-memory carveout for every kernel of a sweep, so that the SMs
+    // are not reconfigured between the cell-list kernels and the phases
+    cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess;
+}
+
+int phase_set_smem_limit(int bytes_needed)
 {
     // the attribute is per kernel, shared by all handles: keep the largest request
     static int granted = 0;
-    const int bytes = std::max(granted, (int)phase_smem_bytes(stencil_cap, warps_per_block));
+    const int bytes = std::max(granted, bytes_needed);
     granted = bytes;
-    cudaError_t e1 = cudaFuncSetAttribute(phase_kernel<MC_PREC_FP64>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    cudaError_t e2 = cudaFuncSetAttribute(phase_kernel<MC_PREC_FP32>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    return (e1 == cudaSuccess && e2 == cudaSuccess) ? 0 : -1;
+    bool ok = true;
+    ok &= set_kernel_smem(phase_kernel<MC_PREC_FP64, 1>, bytes);
+    ok &= set_kernel_smem(phase_kernel<MC_PREC_FP64, 2>, bytes);
+    ok &= set_kernel_smem(phase_kernel<MC_PREC_FP64, 4>, bytes);
+    ok &= set_kernel_smem(phase_kernel<MC_PREC_FP32, 1>, bytes);
+    ok &= set_kernel_smem(phase_kernel<MC_PREC_FP32, 2>, bytes);
+    ok &= set_kernel_smem(phase_kernel<MC_PREC_FP32, 4>, bytes);
+    ok &= set_kernel_smem(sweep_persistent<MC_PREC_FP64, 1>, bytes);
+    ok &= set_kernel_smem(sweep_persistent<MC_PREC_FP64, 2>, bytes);
+    ok &= set_kernel_smem(sweep_persistent<MC_PREC_FP64, 4>, bytes);
+    ok &= set_kernel_smem(sweep_persistent<MC_PREC_FP32, 1>, bytes);
+    ok &= set_kernel_smem(sweep_persistent<MC_PREC_FP32, 2>, bytes);
+    ok &= set_kernel_smem(sweep_persistent<MC_PREC_FP32, 4>, bytes);
+    const int full = cudaSharedmemCarveoutMaxShared;
+    cudaFuncSetAttribute(finalize_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, full);
+    cudaFuncSetAttribute(cl_count_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, full);
+    cudaFuncSetAttribute(cl_scan_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, full);
+    cudaFuncSetAttribute(cl_scatter_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, full);
+    cudaFuncSetAttribute(cl_order_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, full);
+    return ok ? 0 : -1;
 }
 
-void launch_colour_phases(const DevState &d, int buf, int warps_per_block, const LogArgs &lg, cudaStream_t st)
+template <int PREC>
+static void launch_prec(const DevState &d, int buf, int W, const LogArgs &lg, cudaStream_t st)
 {
-    const int blocks = (d.n_act + warps_per_block - 1) / warps_per_block;
-    const size_t sm = phase_smem_bytes(d.stencil_cap, warps_per_block);
+    const int cpb = BLOCK / (32 * W);
+    const int blocks = (d.n_act + cpb - 1) / cpb;
+    const int rec_cap = d.full_rec ? d.stencil_cap : d.own_cap;
+    const size_t sm = phase_smem_bytes(d.stencil_cap, rec_cap, W);
     for (int colour = 0; colour < 8; ++colour) {
-        if (d.precision == MC_PREC_FP64)
-            phase_kernel<MC_PREC_FP64><<<blocks, 32 * warps_per_block, sm, st>>>(d, buf, colour, lg);
-        else
-            phase_kernel<MC_PREC_FP32><<<blocks, 32 * warps_per_block, sm, st>>>(d, buf, colour, lg);
+        if (W == 4) phase_kernel<PREC, 4><<<blocks, BLOCK, sm, st>>>(d, buf, colour, lg);
+        else if (W == 2) phase_kernel<PREC, 2><<<blocks, BLOCK, sm, st>>>(d, buf, colour, lg);
+        else phase_kernel<PREC, 1><<<blocks, BLOCK, sm, st>>>(d, buf, colour, lg);
     }
+}
+
+void launch_colour_phases(const DevState &d, int buf, int warps_per_cell, const LogArgs &lg, cudaStream_t st)
+{
+    if (d.precision == MC_PREC_FP64) launch_prec<MC_PREC_FP64>(d, buf, warps_per_cell, lg, st);
+    else launch_prec<MC_PREC_FP32>(d, buf, warps_per_cell, lg, st);
 }
 
 void launch_finalize(const DevState &d, cudaStream_t st)
 {
-    finalize_kernel<<<d.n_rep, 256, 0, st>>>(d);
+    finalize_kernel<<<d.n_rep, BLOCK, 0, st>>>(d);
 }
 
-void launch_phases(const DevState &d, int buf, int warps_per_block, const LogArgs &lg, cudaStream_t st)
+void launch_phases(const DevState &d, int buf, int warps_per_cell, const LogArgs &lg, cudaStream_t st)
 {
-    launch_colour_phases(d, buf, warps_per_block, lg, st);
+    launch_colour_phases(d, buf, warps_per_cell, lg, st);
     launch_finalize(d, st);
+}
+
+template <int PREC, int W>
+static void *persistent_fn()
+{
+    return (void *)sweep_persistent<PREC, W>;
+}
+
+static void *persistent_kernel(int prec, int W)
+{
+    if (prec == MC_PREC_FP64) return W == 4 ? persistent_fn<MC_PREC_FP64, 4>() : W == 2 ? persistent_fn<MC_PREC_FP64, 2>() : persistent_fn<MC_PREC_FP64, 1>();
+    return W == 4 ? persistent_fn<MC_PREC_FP32, 4>() : W == 2 ? persistent_fn<MC_PREC_FP32, 2>() : persistent_fn<MC_PREC_FP32, 1>();
+}
+
+int persistent_grid(const DevState &d, int warps_per_cell, int max_blocks)
+{
+    int dev = 0, sms = 0, coop = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    if (!coop) return 0;
+    const int rec_cap = d.full_rec ? d.stencil_cap : d.own_cap;
+    const size_t sm = phase_smem_bytes(d.stencil_cap, rec_cap, warps_per_cell);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_kernel(d.precision, warps_per_cell), BLOCK,
+                                                      sm) != cudaSuccess)
+        return 0;
+    const int cpb = BLOCK / (32 * warps_per_cell);
+    const int needed = std::max((d.n_act + cpb - 1) / cpb, sms);
+    return std::max(0, std::min(std::min(per_sm * sms, needed), max_blocks));
+}
+
+int launch_persistent(const DevState &d, int buf, int n_sweeps, int warps_per_cell, int grid, unsigned int *bar,
+                      int *scan_tot, cudaStream_t st)
+{
+    const int rec_cap = d.full_rec ? d.stencil_cap : d.own_cap;
+    const size_t sm = phase_smem_bytes(d.stencil_cap, rec_cap, warps_per_cell);
+    GridBar gb{bar, bar + 1, scan_tot};
+    DevState dd = d;
+    void *args[] = {(void *)&dd, (void *)&buf, (void *)&n_sweeps, (void *)&gb};
+    const cudaError_t e = cudaLaunchCooperativeKernel(persistent_kernel(d.precision, warps_per_cell), dim3(grid),
+                                                      dim3(BLOCK), args, sm, st);
+    return e == cudaSuccess ? 0 : (int)e;
 }
 
 }  // namespace flipmc

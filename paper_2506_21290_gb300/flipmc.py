@@ -49,7 +49,7 @@ class mc_move_mix(C.Structure):
 
 class mc_options(C.Structure):
     _fields_ = [("precision", C.c_int), ("n_cells", C.c_int), ("device", C.c_int), ("stencil_cap", C.c_int),
-                ("recheck_gap", C.c_double)]
+                ("recheck_gap", C.c_double), ("warps_per_cell", C.c_int), ("launch_mode", C.c_int)]
 
 
 class mc_stats(C.Structure):
@@ -60,7 +60,9 @@ class mc_stats(C.Structure):
 
 class mc_info(C.Structure):
     _fields_ = [("n_rep", C.c_int), ("precision", C.c_int), ("stencil_cap", C.c_int), ("total_sites", C.c_int),
-                ("total_cells", C.c_int), ("max_cells_per_axis", C.c_int), ("recheck_gap", C.c_double)]
+                ("total_cells", C.c_int), ("max_cells_per_axis", C.c_int), ("recheck_gap", C.c_double),
+                ("warps_per_cell", C.c_int), ("active_cells_per_colour", C.c_int), ("launch_mode", C.c_int),
+                ("persistent_blocks", C.c_int)]
 
 
 LOG_DTYPE = np.dtype([("site", "<i4"), ("move", "<i2"), ("flags", "<i2"), ("status", "<i4"), ("accepted", "<i4"),
@@ -139,10 +141,13 @@ def make_mix(mix):
     return m
 
 
-def make_options(precision="fp32", n_cells=0, device=0, stencil_cap=0, recheck_gap=0.0):
+def make_options(precision="fp32", n_cells=0, device=0, stencil_cap=0, recheck_gap=0.0, warps_per_cell=0,
+                 launch_mode=0):
     o = mc_options()
     o.precision = PREC[precision] if isinstance(precision, str) else int(precision)
     o.n_cells, o.device, o.stencil_cap, o.recheck_gap = int(n_cells), int(device), int(stencil_cap), float(recheck_gap)
+    o.warps_per_cell = int(warps_per_cell)
+    o.launch_mode = int(launch_mode)
     return o
 
 
@@ -306,8 +311,8 @@ class Handle:
     """One handle of the library (a batch of replicas; one replica by default)."""
 
     def __init__(self, L, xyz, types, pot, precision="fp32", n_cells=0, device=0, stencil_cap=0, recheck_gap=0.0,
-                 n_mol=None):
-        opts = make_options(precision, n_cells, device, stencil_cap, recheck_gap)
+                 n_mol=None, warps_per_cell=0, launch_mode=0):
+        opts = make_options(precision, n_cells, device, stencil_cap, recheck_gap, warps_per_cell, launch_mode)
         if np.ndim(L) == 0:
             self.h = mc_create(L, xyz, types, pot, opts)
         else:

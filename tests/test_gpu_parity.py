@@ -96,11 +96,15 @@ def test_fp64_1000_molecules_bit_exact():
     _compare_state(h, ch)
 
 
-@pytest.mark.parametrize("M,seed,T,mix", [(125, 4, 2.0, W.PAPER_MIX), (216, 5, 0.75, W.RIGID_MIX),
-                                           (64, 6, 3.0, W.PAPER_MIX)])
-def test_fp32_same_decisions_and_dE_within_tolerance(M, seed, T, mix):
-    h, ch = _pair(M, seed, "fp32")
-    ch.run(0, T, mix, seed=seed)
+@pytest.mark.parametrize("M,seed,T,mix,wpc", [(125, 4, 2.0, W.PAPER_MIX, 1), (125, 4, 2.0, W.PAPER_MIX, 2),
+                                               (125, 4, 2.0, W.PAPER_MIX, 4), (216, 5, 0.75, W.RIGID_MIX, 1),
+                                               (216, 5, 0.75, W.RIGID_MIX, 4), (64, 6, 3.0, W.PAPER_MIX, 2),
+                                               (343, 7, 1.1, W.PAPER_MIX, 0)])
+def test_fp32_same_decisions_and_dE_within_tolerance(M, seed, T, mix, wpc):
+    L, xyz, t = _start(M, seed)
+    h = F.Handle(L, xyz, t, POT, precision="fp32", warps_per_cell=wpc)
+    assert wpc == 0 or h.info["warps_per_cell"] == wpc
+    ch = oracle.Chain(L, xyz, t, POT, nc=h.info["max_cells_per_axis"])
     lg = h.sweep_logged(15, T, mix, 7 + seed)
     lo = ch.run(15, T, mix, seed=7 + seed, log=True)
     for f in ("site", "move", "status", "accepted"):
@@ -194,6 +198,29 @@ def test_runs_are_reproducible_and_resumable():
     # positions are cell centres of the grid (q + 1/2) h
     d = F.Handle(L, (q4.astype(np.float64) + 0.5) * (L / 2 ** 32), t4, POT, precision="fp32")
     assert np.array_equal(d.state_fixed()[0], q4)
+
+
+@pytest.mark.parametrize("precision,wpc,M", [("fp64", 1, 125), ("fp32", 1, 343), ("fp32", 2, 343), ("fp32", 4, 1000),
+                                             ("fp64", 4, 216)])
+def test_persistent_launch_matches_graphs(precision, wpc, M):
+    """One cooperative launch for all sweeps of a call gives the same chain,
+    bit for bit, as one CUDA graph per sweep."""
+    L, xyz, t = _start(M, 31)
+    hg = F.Handle(L, xyz, t, POT, precision=precision, warps_per_cell=wpc, launch_mode=1)
+    hp = F.Handle(L, xyz, t, POT, precision=precision, warps_per_cell=wpc, launch_mode=2)
+    for h in (hg, hp):
+        h.sweep(7, 1.3, W.PAPER_MIX, 17)
+        h.sweep(4, 2.0, W.RIGID_MIX, 18)
+    qg, Xg, tg = hg.state_fixed()
+    qp, Xp, tp = hp.state_fixed()
+    assert np.array_equal(qg, qp) and np.array_equal(Xg, Xp) and np.array_equal(tg, tp)
+    sg, sp = hg.stats()[0], hp.stats()[0]
+    assert sg == sp
+    if precision == "fp64":
+        ch = oracle.Chain(L, xyz, t, POT, nc=hp.info["max_cells_per_axis"])
+        ch.run(7, 1.3, W.PAPER_MIX, seed=17)
+        ch.run(4, 2.0, W.RIGID_MIX, seed=18)
+        _compare_state(hp, ch)
 
 
 def test_invalid_inputs_are_rejected():
