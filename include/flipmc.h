@@ -100,7 +100,12 @@ typedef struct {
 /* Creation options.  precision: MC_PREC_FP64 or MC_PREC_FP32.  n_cells: cells
  * per axis (even, >= 2), 0 picks the largest even n_c whose cell side is at
  * least R0 * max bonded sigma_ab (the longest possible interaction).
- * recheck_gap: FP32 decision margin (0 picks 1e-4).  device: CUDA device
+ * recheck_gap: FP32 decision margin as a fraction of the summed term
+ * magnitudes (0 picks 1e-5).  The FP32 Delta E differs from the FP64 one by at
+ * most about 6.3e-6 of that sum (distances to 9 units of FP32 rounding, each
+ * term's sensitivity to them, its own evaluation and the sums), so with the
+ * default every decision taken in FP32 is the one FP64 takes; smaller values
+ * trade that guarantee for fewer FP64 rechecks.  device: CUDA device
  * ordinal.  stencil_cap: atoms staged per cell neighbourhood (0 = automatic).
  * warps_per_cell: 1, 2 or 4 warps per cell, each evaluating one of the cell's
  * consecutive attempts, committed in order (0 = chosen from the number of

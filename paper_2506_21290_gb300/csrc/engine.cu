@@ -77,7 +77,7 @@ struct mc_handle {
     unsigned int *d_bar = nullptr;       // grid barrier words
     int *d_scan_tot = nullptr;           // per-block scan totals of the persistent sweep
     int wpb = 4;
-    double recheck_gap = 1e-4;
+    double recheck_gap = 1e-5;
     mc_params params{};
     std::vector<RepInfo> reps;
     std::vector<int> mol_off;
@@ -341,6 +341,8 @@ int upload_params(mc_handle *h, const double *T, const mc_move_mix *mix, const u
         if (!(t > 0.0) || !std::isfinite(t)) return fail(MC_ERR_INVALID_ARG, "temperature must be positive");
         RepParam &p = h->par_host[r];
         p.T = t;
+        p.T32 = (float)t;
+        p.pad = 0;
         p.seed = same_T_seed ? seeds[0] : seeds[r];
         p.D_atom = fixed_half_width(mix->d_atom, h->reps[r].L);
         p.D_mol = fixed_half_width(mix->d_mol, h->reps[r].L);
@@ -410,7 +412,7 @@ int create_impl(mc_handle **out, int n_rep, const double *L, const int32_t *n_mo
     h->device = o.device;
     h->precision = o.precision;
     h->params = p;
-    h->recheck_gap = o.recheck_gap > 0.0 ? o.recheck_gap : 1e-4;
+    h->recheck_gap = o.recheck_gap > 0.0 ? o.recheck_gap : 1e-5;
     h->n_rep = n_rep;
     build_model(p, h->recheck_gap, h->model_host);
 
@@ -420,9 +422,9 @@ int create_impl(mc_handle **out, int n_rep, const double *L, const int32_t *n_mo
     bool any_small = false;
     std::vector<int> act_off(n_rep + 1, 0), rep_of_site;
     for (int r = 0; r < n_rep; ++r) {
-        if (n_mol[r] < 1) {
+        if (n_mol[r] < 1 || n_mol[r] > kMaxMolecules) {
             delete h;
-            return fail(MC_ERR_INVALID_ARG, "n_mol < 1");
+            return fail(MC_ERR_INVALID_ARG, "n_mol outside [1, 2^27 - 2]");
         }
         if (!(L[r] > 0.0) || !std::isfinite(L[r])) {
             delete h;
@@ -451,6 +453,7 @@ int create_impl(mc_handle **out, int n_rep, const double *L, const int32_t *n_mo
         ri.h = L[r] / kTwo32;
         ri.inv_h = kTwo32 / L[r];
         ri.hf = (float)ri.h;
+        ri.h2f = (float)(ri.h * ri.h);
         h->reps.push_back(ri);
         for (int i = 0; i < ri.n_sites; ++i) rep_of_site.push_back(r);
         sites += ri.n_sites;
@@ -475,7 +478,7 @@ int create_impl(mc_handle **out, int n_rep, const double *L, const int32_t *n_mo
     h->n_cells = (int)cells;
     h->n_act = (int)act;
     // staging capacity: the neighbourhood plus one padding slot, a multiple of 32
-    int cap = o.stencil_cap > 0 ? o.stencil_cap : ((int)std::ceil(max_stencil) + 1 + 31) / 32 * 32;
+    int cap = o.stencil_cap > 0 ? o.stencil_cap : ((int)std::ceil(max_stencil) + kPadSlots + 31) / 32 * 32;
     h->stencil_cap = cap;
     // warps per cell: spread small grids over more warps so that every SM has
     // work; large grids keep one warp per cell (enough cells to fill the GPU)
@@ -644,6 +647,7 @@ static int sweep_impl(mc_handle *h, int n_sweeps, const double *T, const mc_move
         // all sweeps of the call in one cooperative launch (which expects zero
         // cell counts on entry and leaves them zero)
         CUDA_TRY(cudaMemsetAsync(h->ds.cell_count, 0, sizeof(int) * h->n_cells, h->stream));
+        CUDA_TRY(cudaMemsetAsync(h->d_bar, 0, sizeof(unsigned int) * 2, h->stream));
         const int e = launch_persistent(h->ds, h->cur, n_sweeps, h->wpb, h->pgrid, h->d_bar, h->d_scan_tot, h->stream);
         if (e != 0) return fail(MC_ERR_CUDA, std::string("persistent sweep launch: ") + cudaGetErrorString((cudaError_t)e));
         h->cur ^= (n_sweeps & 1);

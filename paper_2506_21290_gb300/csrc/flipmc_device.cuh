@@ -139,14 +139,14 @@ __device__ __forceinline__ void wca32(const ModelDev &md, float r2, int ab, floa
     mag = fmaf(a, s6, a + md.epsf);
 }
 
-// FP32 FENE with its magnitude K eps (|ln(1-x)| + x/(1-x)).
+// FP32 FENE with its magnitude K eps (|ln(1-x)| + x/(1-x) + 1).
 __device__ __forceinline__ void fene32(const ModelDev &md, float r2, int ab, float &u, float &mag)
 {
     const float x = r2 * md.invR2f[ab];
     const float y = 1.0f - x;
     const float l = __logf(y);
     u = md.nkef * l;
-    mag = md.kef * (fabsf(l) + __fdividef(x, y));
+    mag = md.kef * (fabsf(l) + __fdividef(x, y) + 1.0f);
 }
 
 // ---------------------------------------------------------------------------

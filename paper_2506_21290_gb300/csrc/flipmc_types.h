@@ -35,7 +35,7 @@ struct RepInfo {
     int pad;
     double L, h, inv_h;
     float hf;
-    float pad2;
+    float h2f;       // h^2 rounded to FP32
 };
 
 // Per-replica parameters of the current sweep call (written by the host).
@@ -44,6 +44,8 @@ struct RepParam {
     uint64_t seed;
     int32_t D_atom;      // atom step half-width in fixed-point units
     int32_t D_mol;       // molecule step half-width in fixed-point units
+    float T32;           // T rounded to FP32
+    int32_t pad;
 };
 
 // Per-replica counters owned by the device.
@@ -51,6 +53,13 @@ struct RepCtr {
     uint64_t sweep;      // number of the sweep being (or next to be) run
     uint32_t shift[4];   // grid shift of that sweep (x, y, z)
 };
+
+// Staging of a cell neighbourhood: padding candidates after the staged atoms
+// (far away, record word kPadWord: type 0 and a molecule index no atom has,
+// since replicas hold fewer than 2^27 - 1 molecules).
+constexpr int kPadSlots = 4;
+constexpr int kPadWord = 0x7FFFFFF0;
+constexpr int kMaxMolecules = (1 << 27) - 2;
 
 // counters per replica (uint64)
 enum {

@@ -20,8 +20,9 @@
 //   1. candidate pass: each lane takes pairs of candidates from the cell-local
 //      structure-of-arrays coordinates and evaluates old and new squared
 //      distances with packed f32x2 arithmetic (the new one as
-//      r'^2 = r^2 - 2 d.delta + |delta|^2); candidates inside the largest WCA
-//      cutoff, or in the same molecule, are queued in ballot order.
+//      r'^2 = r^2 - 2 d.delta + |delta|^2); candidates inside the screening
+//      radius (r^2 < 1.01 x the largest WCA cutoff squared), or in the same
+//      molecule, are queued in ballot order.  Both modes run this pass.
 //   2. interaction pass over the queue: WCA (Eq. 1) and FENE (Eq. 2), old and
 //      new, in FP32, each with a magnitude that bounds its rounding error.
 //   3. decision: |dE32 - thr32| against gap * sum(magnitudes) plus the error
@@ -37,7 +38,9 @@
 // FP64 mode: every Delta E is the FP64 ordered sum (moved atom ascending, then
 // partner index ascending) of the nonzero pair terms, each operation unfused
 // and rounded to nearest, and the threshold is the FP64 series logarithm; this
-// reproduces the reference FP64 chain exactly.
+// reproduces the reference FP64 chain exactly.  The terms are taken over the
+// queued partners only: the screening radius exceeds every cutoff by far more
+// than the FP32 distance error, so every partner with a nonzero term is queued.
 #include <algorithm>
 #include <cstdio>
 
@@ -51,7 +54,10 @@ constexpr int TERM_CAP = 128;       // nonzero FP64 terms of one move
 constexpr int QW = 64;              // interaction queue entries per warp
 constexpr int BLOCK = 128;          // threads per block (all W)
 constexpr unsigned FULL = 0xffffffffu;
-constexpr float FAR = 1.0e18f;      // coordinate of the padding candidate
+constexpr float FAR = 1.0e18f;      // coordinate of the padding candidates (fixed-point units)
+constexpr int PADS = kPadSlots;     // padding candidates staged after the K atoms
+constexpr int PAD_W = kPadWord;     // their record word: type 0, a molecule no atom has
+constexpr int SCREEN_U = 4;         // 64-candidate steps per screening block
 
 // ---------------------------------------------------------------------------
 // packed FP32 pairs (f32x2, sm_100 and later)
@@ -87,13 +93,57 @@ __device__ __forceinline__ f2_t fma2(f2_t a, f2_t b, f2_t c)
     return r;
 }
 
-struct PosF {
-    float x, y, z;
-};
-
 struct Q3 {
     uint32_t x, y, z;
 };
+
+// ---------------------------------------------------------------------------
+// Cell-local coordinates.  A staged atom's position relative to the cell
+// centre P is the int32 X = q - P in fixed-point units (|X| < 2^31 when
+// n_c >= 4).  It is kept as X = H + l with H a multiple of 256 and 0 <= l < 256:
+// H is exact in FP32 (at most 23 significant bits), and so is the difference
+// of two H (a multiple of 256 below 2^32), so a distance built from H
+// differences only carries the rounding of its own squares and sums.  The low
+// bytes l are added back for the pairs that enter Delta E.
+// ---------------------------------------------------------------------------
+struct HiLo {
+    float x, y, z;   // H per axis
+    int lo;          // l per axis, packed x | y << 8 | z << 16
+};
+
+__device__ __forceinline__ HiLo make_hilo(int X, int Y, int Z)
+{
+    HiLo r;
+    r.x = (float)(X & ~255);
+    r.y = (float)(Y & ~255);
+    r.z = (float)(Z & ~255);
+    r.lo = (X & 255) | ((Y & 255) << 8) | ((Z & 255) << 16);
+    return r;
+}
+
+// byte b of a packed word as the float 2^23 + b (integer OR, no conversion):
+// the difference of two such values is the exact difference of the bytes
+__device__ __forceinline__ float lo_f(int lo, int sh) { return __int_as_float(0x4B000000 | ((lo >> sh) & 255)); }
+
+// squared distance in fixed-point units squared: exact H differences plus exact
+// l differences, one rounding per axis, then the squares and sums
+__device__ __forceinline__ float r2_acc(float X, float Y, float Z, int lo, const HiLo &o)
+{
+    const float ex = (X - o.x) + (lo_f(lo, 0) - lo_f(o.lo, 0));
+    const float ey = (Y - o.y) + (lo_f(lo, 8) - lo_f(o.lo, 8));
+    const float ez = (Z - o.z) + (lo_f(lo, 16) - lo_f(o.lo, 16));
+    return fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+}
+
+// squared distance from raw fixed-point records (any n_c): int32 differences
+// (the minimum image), converted and scaled by h
+__device__ __forceinline__ float r2_int32f(const int4 &r, const Q3 b, float hf)
+{
+    const float dx = (float)(int)((uint32_t)r.x - b.x) * hf;
+    const float dy = (float)(int)((uint32_t)r.y - b.y) * hf;
+    const float dz = (float)(int)((uint32_t)r.z - b.z) * hf;
+    return fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+}
 
 // ---------------------------------------------------------------------------
 // shared memory
@@ -101,57 +151,73 @@ struct Q3 {
 
 // per warp: interaction queue, and (aliased, used after it) the FP64 term buffers
 struct WarpScr {
-    int *qc;                    // [QW]
-    float *qr;                  // [6 * QW]
+    int *qc;                    // [QW + 1] queued candidate indices, then a slot that takes discarded writes
     unsigned long long *key;    // [TERM_CAP]
     double *val;                // [TERM_CAP]
     double *sorted;             // [TERM_CAP]
     int *cnt;                   // [4]
 };
 
-// the outcome of one evaluated attempt, for the in-order commit
+// the outcome of one evaluated attempt (registers of the evaluating warp,
+// which also commits it)
 struct Res {
-    int status, accept, flags, mvt, nmv, site, mol, nat;
+    int status, accept, flags, mvt, nmv, site, mol;
     int ks[3], t3n[3];
     uint32_t qn[3][3];
-    float px[6], py[6], pz[6];  // atoms of the move (old and new positions), cell-local
-    double dE_used;             // Delta E added to the running energy if accepted
-    double dE_log;              // Delta E as the mode computed it
-    double dE64;
-    float scale;
+    HiLo hn[3];                 // new positions of the moved atoms, split as staged
+    float dE32;                 // FP32 mode: the FP32 Delta E
+    float scale;                // FP32 mode: sum of the term magnitudes
+    double dE64;                // the FP64 Delta E (FP64 mode, or an FP32-mode recheck), else NaN
     int pairs;                  // site-pair evaluations per candidate (2 or 6)
 };
 
+// what the conflict test of the later attempts of a round reads (W > 1)
+struct Near {
+    int accept, mol, nat, pad;
+    float px[6], py[6], pz[6];  // H of the move's atoms (old and new)
+};
+
+// attempt counts of one warp over one cell
+struct Tally {
+    unsigned att[4], acc[4], rej_geom, rej_bond, rechecks;
+    float dEf;                  // FP32 mode: accepted Delta E, in commit order
+    unsigned long long pairs;
+    double dE;                  // FP64 mode: accepted Delta E, in commit order
+};
+
 struct Group {
-    float *sx, *sy, *sz;        // [cap] cell-local FP32 coordinates
+    float *sx, *sy, *sz;        // [cap] H of the staged atoms (fixed-point units)
+    int *sl;                    // [cap] their packed low bytes
     int *sw;                    // [cap] record words
-    int4 *rec;                  // [cap or own_cap] raw records {qx, qy, qz, w}, own cell first
+    int4 *rec;                  // [rec_cap] raw records {qx, qy, qz, w}, own cell first
+    int4 *orig;                 // [rec_cap] the own cell as staged (periodic images at write-back)
     uint32_t *rnd;              // [32 * 8] random words of a chunk of attempts
     double *thr64;              // [32]
     float *thr32;               // [32]
     int *cstart;                // [32]
     int *coff;                  // [32]
-    int *misc;                  // [16]
-    Res *res;                   // [W]
+    int *misc;                  // [32]
+    Near *near;                 // [W]
+    Tally *tally;               // [W]
     unsigned char *warp_base;   // W per-warp scratch blocks
 };
 
-enum { MS_K = 0, MS_N = 1, MS_START = 2, MS_ADV = 3 };
+enum { MS_K = 0, MS_N = 1, MS_START = 2, MS_CLASH = 4 };
 
 __host__ __device__ constexpr size_t al16(size_t x) { return (x + 15) & ~size_t(15); }
 
 __host__ __device__ inline size_t warp_scr_bytes()
 {
-    const size_t q = al16(sizeof(int) * QW) + al16(sizeof(float) * 6 * QW);
-    const size_t t = al16(sizeof(unsigned long long) * TERM_CAP) + 2 * al16(sizeof(double) * TERM_CAP);
-    return (q > t ? q : t) + al16(sizeof(int) * 4);
+    const size_t q = al16(sizeof(int) * (QW + 1));
+    const size_t k = al16(sizeof(unsigned long long) * TERM_CAP);
+    return (q > k ? q : k) + 2 * al16(sizeof(double) * TERM_CAP) + al16(sizeof(int) * 4);
 }
 
 __host__ __device__ inline size_t group_bytes(int cap, int rec_cap, int W)
 {
-    return 4 * al16(sizeof(float) * cap) + al16(sizeof(int4) * rec_cap) + al16(sizeof(uint32_t) * 256) +
+    return 5 * al16(sizeof(float) * cap) + 2 * al16(sizeof(int4) * rec_cap) + al16(sizeof(uint32_t) * 256) +
            al16(sizeof(double) * 32) + al16(sizeof(float) * 32) + 3 * al16(sizeof(int) * 32) +
-           al16(sizeof(Res) * W) + (size_t)W * warp_scr_bytes();
+           al16(sizeof(Near) * W) + al16(sizeof(Tally) * W) + (size_t)W * warp_scr_bytes();
 }
 
 __device__ inline Group carve(unsigned char *base, int cap, int rec_cap, int W)
@@ -166,15 +232,18 @@ __device__ inline Group carve(unsigned char *base, int cap, int rec_cap, int W)
     s.sx = (float *)take(sizeof(float) * cap);
     s.sy = (float *)take(sizeof(float) * cap);
     s.sz = (float *)take(sizeof(float) * cap);
+    s.sl = (int *)take(sizeof(int) * cap);
     s.sw = (int *)take(sizeof(int) * cap);
     s.rec = (int4 *)take(sizeof(int4) * rec_cap);
+    s.orig = (int4 *)take(sizeof(int4) * rec_cap);
     s.rnd = (uint32_t *)take(sizeof(uint32_t) * 256);
     s.thr64 = (double *)take(sizeof(double) * 32);
     s.thr32 = (float *)take(sizeof(float) * 32);
     s.cstart = (int *)take(sizeof(int) * 32);
     s.coff = (int *)take(sizeof(int) * 32);
     s.misc = (int *)take(sizeof(int) * 32);
-    s.res = (Res *)take(sizeof(Res) * W);
+    s.near = (Near *)take(sizeof(Near) * W);
+    s.tally = (Tally *)take(sizeof(Tally) * W);
     s.warp_base = base + o;
     return s;
 }
@@ -183,14 +252,14 @@ __device__ inline WarpScr warp_scr(const Group &G, int wig)
 {
     unsigned char *b = G.warp_base + (size_t)wig * warp_scr_bytes();
     WarpScr s;
+    const size_t q = al16(sizeof(int) * (QW + 1));
+    const size_t k = al16(sizeof(unsigned long long) * TERM_CAP);
+    const size_t qk = q > k ? q : k;
     s.qc = (int *)b;
-    s.qr = (float *)(b + al16(sizeof(int) * QW));
     s.key = (unsigned long long *)b;    // aliases the queue: used only after it
-    s.val = (double *)(b + al16(sizeof(unsigned long long) * TERM_CAP));
-    s.sorted = (double *)(b + al16(sizeof(unsigned long long) * TERM_CAP) + al16(sizeof(double) * TERM_CAP));
-    const size_t q = al16(sizeof(int) * QW) + al16(sizeof(float) * 6 * QW);
-    const size_t t = al16(sizeof(unsigned long long) * TERM_CAP) + 2 * al16(sizeof(double) * TERM_CAP);
-    s.cnt = (int *)(b + (q > t ? q : t));
+    s.val = (double *)(b + qk);
+    s.sorted = (double *)(b + qk + al16(sizeof(double) * TERM_CAP));
+    s.cnt = (int *)(b + qk + 2 * al16(sizeof(double) * TERM_CAP));
     return s;
 }
 
@@ -247,18 +316,32 @@ struct Move {
 // FP64 ordered Delta E of a move, one warp (all lanes return the same value).
 // Returns MC_ST_EVALUATED or MC_ST_BOND_BREAK.
 // ---------------------------------------------------------------------------
-__device__ __noinline__ int dE64_ordered(const Move &mv, const RecView &rv, const WarpScr &S, int K, const ModelDev &md,
-                                         double h, float hf, float pre_r2, int lane, int *err, double &dE)
+// The candidates are the nq queued ones of the FP32 candidate pass when
+// nq >= 0 (the queue holds every partner within the screening radius and every
+// atom of the molecule, so no nonzero term is missed), else all K staged atoms.
+// Terms are keyed by (moved atom, partner site), so which lane computes a term
+// does not change the sum.
+__device__ __noinline__ int dE64_ordered(const Move &mv, const RecView rv, const WarpScr S, int K, int nq,
+                                         const ModelDev &md, double h, float hf, float pre_r2, int lane, int *err,
+                                         double &dE)
 {
+    static_assert(QW <= 64, "a lane takes at most two queue entries");
+    // the term buffers alias the queue: take the entries into registers first
+    int qe0 = -1, qe1 = -1;
+    if (nq >= 0) {
+        if (lane < nq) qe0 = S.qc[lane];
+        if (lane + 32 < nq) qe1 = S.qc[lane + 32];
+    }
+    __syncwarp();
     if (lane == 0) S.cnt[0] = 0;
     __syncwarp();
     int brk = 0;
-    for (int c = lane; c < K; c += 32) {
+    auto term_of = [&](int c) {
         const int4 r = rv.at(c);
         const int sj = rec_site(r.w);
         bool in_set = false;
         for (int k = 0; k < mv.n; ++k) in_set |= (sj == mv.site[k]);
-        if (in_set) continue;
+        if (in_set) return;
         const bool bonded = rec_mol(r.w) == mv.mol;
         const int tj = rec_type(r.w);
         for (int k = 0; k < mv.n; ++k) {
@@ -289,6 +372,12 @@ __device__ __noinline__ int dE64_ordered(const Move &mv, const RecView &rv, cons
                 }
             }
         }
+    };
+    if (nq >= 0) {
+        if (qe0 >= 0) term_of(qe0);
+        if (qe1 >= 0) term_of(qe1);
+    } else {
+        for (int c = lane; c < K; c += 32) term_of(c);
     }
     if (mv.intra && lane == 0) {
         const int pk3[3] = {0, 0, 1}, pl3[3] = {1, 2, 2};
@@ -373,201 +462,165 @@ __device__ __noinline__ void rotate_molecule(const uint32_t (*q)[3], uint32_t (*
     }
 }
 
+
 // ---------------------------------------------------------------------------
-// FP32 candidate passes: fill the warp's interaction queue
+// Candidate screens: queue every partner within the screening radius of an
+// old or new position of a moved atom (and, for single-atom moves and flips,
+// every atom of the molecule).  The loads and the arithmetic of U steps of 64
+// candidates are issued before any queue store, and the queue is filled in
+// ballot order afterwards; entries past QW are counted but not stored.
 // ---------------------------------------------------------------------------
 
-// warp-aggregated append, ballot order; entries past QW are counted but not
-// stored (the caller then decides in FP64).  r2 value j of entry e is qr[j*QW+e].
-template <int NV>
-__device__ __forceinline__ void push2(const WarpScr &S, int lane, int &qlen, bool p0, int c0, const float *v0, bool p1,
-                                      int c1, const float *v1)
+// append the hits of one 64-candidate step (candidate c = base + 2 lane for
+// bit b0, c + 1 for b1) in ballot order.  Every lane stores: lanes without a
+// hit, and hits past QW, write the discard slot, so the warp never diverges.
+__device__ __forceinline__ void queue_step(const WarpScr &S, int lane, int &qlen, unsigned b0, unsigned b1, int c)
 {
-    const unsigned b0 = __ballot_sync(FULL, p0), b1 = __ballot_sync(FULL, p1);
-    const int base = qlen;
-    qlen += __popc(b0) + __popc(b1);
     const unsigned lt = (1u << lane) - 1u;
-    if (p0) {
-        const int e = base + __popc(b0 & lt);
-        if (e < QW) {
-            S.qc[e] = c0;
-#pragma unroll
-            for (int j = 0; j < NV; ++j) S.qr[j * QW + e] = v0[j];
-        }
-    }
-    if (p1) {
-        const int e = base + __popc(b0) + __popc(b1 & lt);
-        if (e < QW) {
-            S.qc[e] = c1;
-#pragma unroll
-            for (int j = 0; j < NV; ++j) S.qr[j * QW + e] = v1[j];
-        }
-    }
+    const int e0 = ((b0 >> lane) & 1u) ? min(qlen + __popc(b0 & lt), QW) : QW;
+    const int e1 = ((b1 >> lane) & 1u) ? min(qlen + __popc(b0) + __popc(b1 & lt), QW) : QW;
+    S.qc[e0] = c;
+    S.qc[e1] = c + 1;
+    qlen += __popc(b0) + __popc(b1);
 }
 
-__device__ __forceinline__ float r2_int32f(const int4 &r, const Q3 b, float hf)
+// Atom translation from o to nn (H parts): the old distance, and the new one
+// as r'^2 = r^2 - 2 d.e + |d|^2, in packed FP32 pairs.
+__device__ __forceinline__ int screen_atom(const Group &G, const WarpScr &S, int K, int lane, const HiLo &o,
+                                           const HiLo &nn, int wi, float r2q)
 {
-    const float dx = (float)(int)((uint32_t)r.x - b.x) * hf;
-    const float dy = (float)(int)((uint32_t)r.y - b.y) * hf;
-    const float dz = (float)(int)((uint32_t)r.z - b.z) * hf;
-    return fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-}
-
-// Atom translation: old and new distance to every candidate.
-__device__ __forceinline__ int pass_atom(const Group &G, const WarpScr &S, int K, int lane, bool small, const PosF so,
-                                         const PosF sn, int wi, const Q3 qo, const Q3 qn, float hf, float rc2max)
-{
+    const float dx = nn.x - o.x, dy = nn.y - o.y, dz = nn.z - o.z;   // exact
+    const f2_t nxo = pk(-o.x, -o.x), nyo = pk(-o.y, -o.y), nzo = pk(-o.z, -o.z);
+    const f2_t mx = pk(-2.f * dx, -2.f * dx), my = pk(-2.f * dy, -2.f * dy), mz = pk(-2.f * dz, -2.f * dz);
+    const float dd = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    const f2_t d2 = pk(dd, dd);
+    const int cpad = (K + 1) & ~1;   // an even index whose pair is padding
     int qlen = 0;
-    if (!small) {
-        const float dx = sn.x - so.x, dy = sn.y - so.y, dz = sn.z - so.z;
-        const f2_t nxo = pk(-so.x, -so.x), nyo = pk(-so.y, -so.y), nzo = pk(-so.z, -so.z);
-        const f2_t mx = pk(-2.f * dx, -2.f * dx), my = pk(-2.f * dy, -2.f * dy), mz = pk(-2.f * dz, -2.f * dz);
-        const float dd = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        const f2_t d2 = pk(dd, dd);
-        for (int base = 0; base < K; base += 64) {
-            const int c = base + 2 * lane;
-            bool p0 = false, p1 = false;
-            float v0[2] = {0.f, 0.f}, v1[2] = {0.f, 0.f};
-            if (c < K) {
-                const f2_t X = *(const f2_t *)(G.sx + c);
-                const f2_t Y = *(const f2_t *)(G.sy + c);
-                const f2_t Z = *(const f2_t *)(G.sz + c);
-                const int2 ww = *(const int2 *)(G.sw + c);
-                const f2_t ex = add2(X, nxo), ey = add2(Y, nyo), ez = add2(Z, nzo);
-                const f2_t r2o = fma2(ez, ez, fma2(ey, ey, mul2(ex, ex)));
-                const f2_t r2n = fma2(ez, mz, fma2(ey, my, fma2(ex, mx, add2(r2o, d2))));
-                upk(r2o, v0[0], v1[0]);
-                upk(r2n, v0[1], v1[1]);
-                p0 = (fminf(v0[0], v0[1]) < rc2max) | ((ww.x ^ wi) < 16);
-                p1 = (fminf(v1[0], v1[1]) < rc2max) | ((ww.y ^ wi) < 16);
-            }
-            push2<2>(S, lane, qlen, p0, c, v0, p1, c + 1, v1);
+    for (int base = 0; base < K; base += 64 * SCREEN_U) {
+        unsigned b0[SCREEN_U], b1[SCREEN_U];
+#pragma unroll
+        for (int u = 0; u < SCREEN_U; ++u) {
+            const int c = base + 64 * u + 2 * lane;
+            const int cl = c < K ? c : cpad;   // past the end: the padding pair (far, no molecule)
+            const f2_t X = *(const f2_t *)(G.sx + cl);
+            const f2_t Y = *(const f2_t *)(G.sy + cl);
+            const f2_t Z = *(const f2_t *)(G.sz + cl);
+            const int2 ww = *(const int2 *)(G.sw + cl);
+            const f2_t ex = add2(X, nxo), ey = add2(Y, nyo), ez = add2(Z, nzo);
+            const f2_t r2o = fma2(ez, ez, fma2(ey, ey, mul2(ex, ex)));
+            const f2_t r2n = fma2(ez, mz, fma2(ey, my, fma2(ex, mx, add2(r2o, d2))));
+            float a0, a1, n0, n1;
+            upk(r2o, a0, a1);
+            upk(r2n, n0, n1);
+            const bool p0 = (fminf(a0, n0) < r2q) | ((ww.x ^ wi) < 16);
+            const bool p1 = (fminf(a1, n1) < r2q) | ((ww.y ^ wi) < 16);
+            b0[u] = __ballot_sync(FULL, p0);
+            b1[u] = __ballot_sync(FULL, p1);
         }
-    } else {
-        for (int base = 0; base < K; base += 64) {
-            const int c = base + 2 * lane;
-            bool p0 = false, p1 = false;
-            float v0[2] = {0.f, 0.f}, v1[2] = {0.f, 0.f};
-            if (c < K) {
-                const int4 r = G.rec[c];
-                v0[0] = r2_int32f(r, qo, hf);
-                v0[1] = r2_int32f(r, qn, hf);
-                p0 = (fminf(v0[0], v0[1]) < rc2max) | ((r.w ^ wi) < 16);
-            }
-            if (c + 1 < K) {
-                const int4 r = G.rec[c + 1];
-                v1[0] = r2_int32f(r, qo, hf);
-                v1[1] = r2_int32f(r, qn, hf);
-                p1 = (fminf(v1[0], v1[1]) < rc2max) | ((r.w ^ wi) < 16);
-            }
-            push2<2>(S, lane, qlen, p0, c, v0, p1, c + 1, v1);
-        }
+#pragma unroll
+        for (int u = 0; u < SCREEN_U; ++u) queue_step(S, lane, qlen, b0[u], b1[u], base + 64 * u + 2 * lane);
     }
     return qlen;
 }
 
 // Flip: distance of every candidate to the two atoms whose types swap.
-__device__ __forceinline__ int pass_flip(const Group &G, const WarpScr &S, int K, int lane, bool small, const PosF sp,
-                                         const PosF sq, int wi, const Q3 qp, const Q3 qq, float hf, float rc2max)
+__device__ __forceinline__ int screen_flip(const Group &G, const WarpScr &S, int K, int lane, const HiLo &hp,
+                                           const HiLo &hq, int wi, float r2q)
 {
+    const f2_t npx = pk(-hp.x, -hp.x), npy = pk(-hp.y, -hp.y), npz = pk(-hp.z, -hp.z);
+    const f2_t nqx = pk(-hq.x, -hq.x), nqy = pk(-hq.y, -hq.y), nqz = pk(-hq.z, -hq.z);
+    const int cpad = (K + 1) & ~1;
     int qlen = 0;
-    if (!small) {
-        const f2_t npx = pk(-sp.x, -sp.x), npy = pk(-sp.y, -sp.y), npz = pk(-sp.z, -sp.z);
-        const f2_t nqx = pk(-sq.x, -sq.x), nqy = pk(-sq.y, -sq.y), nqz = pk(-sq.z, -sq.z);
-        for (int base = 0; base < K; base += 64) {
-            const int c = base + 2 * lane;
-            bool p0 = false, p1 = false;
-            float v0[2] = {0.f, 0.f}, v1[2] = {0.f, 0.f};
-            if (c < K) {
-                const f2_t X = *(const f2_t *)(G.sx + c);
-                const f2_t Y = *(const f2_t *)(G.sy + c);
-                const f2_t Z = *(const f2_t *)(G.sz + c);
-                const int2 ww = *(const int2 *)(G.sw + c);
-                f2_t ex = add2(X, npx), ey = add2(Y, npy), ez = add2(Z, npz);
-                const f2_t rp = fma2(ez, ez, fma2(ey, ey, mul2(ex, ex)));
-                ex = add2(X, nqx);
-                ey = add2(Y, nqy);
-                ez = add2(Z, nqz);
-                const f2_t rq = fma2(ez, ez, fma2(ey, ey, mul2(ex, ex)));
-                upk(rp, v0[0], v1[0]);
-                upk(rq, v0[1], v1[1]);
-                p0 = (fminf(v0[0], v0[1]) < rc2max) | ((ww.x ^ wi) < 16);
-                p1 = (fminf(v1[0], v1[1]) < rc2max) | ((ww.y ^ wi) < 16);
-            }
-            push2<2>(S, lane, qlen, p0, c, v0, p1, c + 1, v1);
+    for (int base = 0; base < K; base += 64 * SCREEN_U) {
+        unsigned b0[SCREEN_U], b1[SCREEN_U];
+#pragma unroll
+        for (int u = 0; u < SCREEN_U; ++u) {
+            const int c = base + 64 * u + 2 * lane;
+            const int cl = c < K ? c : cpad;
+            const f2_t X = *(const f2_t *)(G.sx + cl);
+            const f2_t Y = *(const f2_t *)(G.sy + cl);
+            const f2_t Z = *(const f2_t *)(G.sz + cl);
+            const int2 ww = *(const int2 *)(G.sw + cl);
+            f2_t ex = add2(X, npx), ey = add2(Y, npy), ez = add2(Z, npz);
+            const f2_t rp = fma2(ez, ez, fma2(ey, ey, mul2(ex, ex)));
+            ex = add2(X, nqx);
+            ey = add2(Y, nqy);
+            ez = add2(Z, nqz);
+            const f2_t rq = fma2(ez, ez, fma2(ey, ey, mul2(ex, ex)));
+            float a0, a1, n0, n1;
+            upk(rp, a0, a1);
+            upk(rq, n0, n1);
+            const bool p0 = (fminf(a0, n0) < r2q) | ((ww.x ^ wi) < 16);
+            const bool p1 = (fminf(a1, n1) < r2q) | ((ww.y ^ wi) < 16);
+            b0[u] = __ballot_sync(FULL, p0);
+            b1[u] = __ballot_sync(FULL, p1);
         }
-    } else {
-        for (int base = 0; base < K; base += 64) {
-            const int c = base + 2 * lane;
-            bool p0 = false, p1 = false;
-            float v0[2] = {0.f, 0.f}, v1[2] = {0.f, 0.f};
-            if (c < K) {
-                const int4 r = G.rec[c];
-                v0[0] = r2_int32f(r, qp, hf);
-                v0[1] = r2_int32f(r, qq, hf);
-                p0 = (fminf(v0[0], v0[1]) < rc2max) | ((r.w ^ wi) < 16);
-            }
-            if (c + 1 < K) {
-                const int4 r = G.rec[c + 1];
-                v1[0] = r2_int32f(r, qp, hf);
-                v1[1] = r2_int32f(r, qq, hf);
-                p1 = (fminf(v1[0], v1[1]) < rc2max) | ((r.w ^ wi) < 16);
-            }
-            push2<2>(S, lane, qlen, p0, c, v0, p1, c + 1, v1);
-        }
+#pragma unroll
+        for (int u = 0; u < SCREEN_U; ++u) queue_step(S, lane, qlen, b0[u], b1[u], base + 64 * u + 2 * lane);
     }
     return qlen;
 }
 
-// Rigid molecule move: old and new distances of the three atoms.
-__device__ __noinline__ int pass_mol(const Group &G, const WarpScr &S, int K, int lane, bool small, const PosF *so,
-                                     const PosF *sn, int wi, const Q3 *qo, const Q3 *qn, float hf, float rc2max)
+// Rigid molecule move: the three atoms, old and new (molecule partners are
+// not queued: their distances do not change).
+__device__ __noinline__ int screen_mol(const Group G, const WarpScr S, int K, int lane, const HiLo *ho,
+                                       const HiLo *hn, int wi, float r2q)
 {
     int qlen = 0;
     for (int base = 0; base < K; base += 64) {
         bool pp[2] = {false, false};
-        float v[2][6];
 #pragma unroll
         for (int hh = 0; hh < 2; ++hh) {
             const int c = base + 2 * lane + hh;
-#pragma unroll
-            for (int j = 0; j < 6; ++j) v[hh][j] = 0.f;
             if (c < K) {
-                int w;
-                if (small) {
-                    const int4 r = G.rec[c];
-                    w = r.w;
+                const float x = G.sx[c], y = G.sy[c], z = G.sz[c];
+                float mn = 3.0e38f;
 #pragma unroll
-                    for (int s = 0; s < 3; ++s) {
-                        v[hh][s] = r2_int32f(r, qo[s], hf);
-                        v[hh][3 + s] = r2_int32f(r, qn[s], hf);
-                    }
-                } else {
-                    const float x = G.sx[c], y = G.sy[c], z = G.sz[c];
-                    w = G.sw[c];
-#pragma unroll
-                    for (int s = 0; s < 3; ++s) {
-                        float ex = x - so[s].x, ey = y - so[s].y, ez = z - so[s].z;
-                        v[hh][s] = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-                        ex = x - sn[s].x;
-                        ey = y - sn[s].y;
-                        ez = z - sn[s].z;
-                        v[hh][3 + s] = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-                    }
+                for (int s = 0; s < 3; ++s) {
+                    float ex = x - ho[s].x, ey = y - ho[s].y, ez = z - ho[s].z;
+                    mn = fminf(mn, fmaf(ex, ex, fmaf(ey, ey, ez * ez)));
+                    ex = x - hn[s].x;
+                    ey = y - hn[s].y;
+                    ez = z - hn[s].z;
+                    mn = fminf(mn, fmaf(ex, ex, fmaf(ey, ey, ez * ez)));
                 }
-                float mn = v[hh][0];
-#pragma unroll
-                for (int j = 1; j < 6; ++j) mn = fminf(mn, v[hh][j]);
-                pp[hh] = (mn < rc2max) && ((w ^ wi) >= 16);
+                pp[hh] = (mn < r2q) && ((G.sw[c] ^ wi) >= 16);
             }
         }
-        push2<6>(S, lane, qlen, pp[0], base + 2 * lane, v[0], pp[1], base + 2 * lane + 1, v[1]);
+        queue_step(S, lane, qlen, __ballot_sync(FULL, pp[0]), __ballot_sync(FULL, pp[1]), base + 2 * lane);
+    }
+    return qlen;
+}
+
+// n_c = 2 boxes: distances from the raw records (the neighbourhood wraps onto
+// itself, so each pair takes its own minimum image).  npos positions; for a
+// rigid move (mol_move) the molecule is excluded, else always included.
+__device__ __noinline__ int screen_raw(const Group G, const WarpScr S, int K, int lane, const Q3 *pos, int npos,
+                                       int wi, bool mol_move, float hf, float r2q)
+{
+    int qlen = 0;
+    for (int base = 0; base < K; base += 64) {
+        bool pp[2] = {false, false};
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+            const int c = base + 2 * lane + hh;
+            if (c < K) {
+                const int4 r = G.rec[c];
+                float mn = 3.0e38f;
+                for (int s = 0; s < npos; ++s) mn = fminf(mn, r2_int32f(r, pos[s], hf));
+                const bool same = (r.w ^ wi) < 16;
+                pp[hh] = mol_move ? ((mn < r2q) && !same) : ((mn < r2q) || same);
+            }
+        }
+        queue_step(S, lane, qlen, __ballot_sync(FULL, pp[0]), __ballot_sync(FULL, pp[1]), base + 2 * lane);
     }
     return qlen;
 }
 
 // ---------------------------------------------------------------------------
-// FP32 interaction passes over the queue: partial (dE, mag, guard) per lane
+// FP32 interaction passes over the queue (each lane takes entries lane and
+// lane + 32): partial (dE, mag, guard) per lane.  Distances are recomputed
+// accurately from the staged coordinates (H and l, or the raw records).
 // ---------------------------------------------------------------------------
 struct Acc32 {
     float dE, mag;
@@ -596,71 +649,151 @@ __device__ __forceinline__ void add_fene(const ModelDev &md, float r2, int ab, f
     a.mag += m;
 }
 
+// Masked forms for the hot passes: every lane evaluates every term and
+// multiplies it by 0 or 1, so the warp never diverges (in a latency-bound warp
+// a divergent branch costs more than the arithmetic it skips).  Terms that are
+// on add exactly what add_wca / add_fene add.
+__device__ __forceinline__ void wca_m(const ModelDev &md, float r2, int ab, float sign, Acc32 &a)
+{
+    float u, m;
+    wca32(md, r2, ab, u, m);
+    const float on = r2 < md.rc2f[ab] ? 1.f : 0.f;
+    a.dE = fmaf(sign * on, u, a.dE);
+    a.mag = fmaf(on, m, a.mag);
+}
+
+__device__ __forceinline__ void fene_m(const ModelDev &md, float r2, int ab, float sign, bool bonded, Acc32 &a)
+{
+    const float x = r2 * md.invR2f[ab];
+    const bool stretched = x >= md.bond_guard_f;
+    a.guard |= (bonded && stretched) ? 1 : 0;
+    const bool on = bonded && !stretched;
+    const float xs = on ? x : 0.f;
+    const float y = 1.0f - xs;
+    const float l = __logf(y);
+    const float f = on ? 1.f : 0.f;
+    a.dE = fmaf(sign * f, md.nkef * l, a.dE);
+    a.mag = fmaf(f, md.kef * (fabsf(l) + __fdividef(xs, y) + 1.0f), a.mag);
+}
+
+// one queued candidate as the interaction passes need it
+struct Cand {
+    float X, Y, Z;
+    int lo;
+    int4 r;
+    int w;
+};
+
+__device__ __forceinline__ Cand load_cand(const Group &G, bool raw, int c)
+{
+    Cand d;
+    if (raw) {
+        d.r = G.rec[c];
+        d.w = d.r.w;
+        d.X = d.Y = d.Z = 0.f;
+        d.lo = 0;
+    } else {
+        d.X = G.sx[c];
+        d.Y = G.sy[c];
+        d.Z = G.sz[c];
+        d.lo = G.sl[c];
+        d.w = G.sw[c];
+        d.r = make_int4(0, 0, 0, 0);
+    }
+    return d;
+}
+
+// squared distance (sigma units) of a candidate to a moved atom's position;
+// a padding candidate is beyond every cutoff
+__device__ __forceinline__ float cand_r2(const Cand &d, bool raw, const HiLo &h, const Q3 &q, float hf, float h2)
+{
+    const float r2 = raw ? r2_int32f(d.r, q, hf) : r2_acc(d.X, d.Y, d.Z, d.lo, h) * h2;
+    return d.w == PAD_W ? 1.0e30f : r2;
+}
+
+// Entry e of the queue, or the padding candidate cpad when e is past the
+// queue or names one of the moved atoms.
+__device__ __forceinline__ int queued(const WarpScr &S, int e, int nq, int cpad, int k0, int k1)
+{
+    const int cq = S.qc[e];   // e < QW: inside the queue array
+    return (e < nq && cq != k0 && cq != k1) ? cq : cpad;
+}
+
 __device__ __forceinline__ Acc32 inter_atom(const Group &G, const WarpScr &S, int nq, int lane, const ModelDev &md,
-                                            int k, int wi, int ti)
+                                            bool raw, int k, int cpad, int wi, int ti, const HiLo &ho, const HiLo &hn,
+                                            const Q3 &qo, const Q3 &qn, float hf, float h2)
 {
     Acc32 a{0.f, 0.f, 0};
-    for (int e = lane; e < nq; e += 32) {
-        const int c = S.qc[e];
-        if (c == k) continue;
-        const int wj = G.sw[c];
-        const int ab = 3 * ti + rec_type(wj);
-        const float r2o = S.qr[e], r2n = S.qr[QW + e];
-        add_wca(md, r2o, ab, -1.f, a);
-        add_wca(md, r2n, ab, 1.f, a);
-        if ((wj ^ wi) < 16) {
-            add_fene(md, r2o, ab, -1.f, a);
-            add_fene(md, r2n, ab, 1.f, a);
+    const int slots = nq > 32 ? 2 : 1;   // warp-uniform
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        if (s < slots) {
+            const int c = queued(S, lane + 32 * s, nq, cpad, k, k);
+            const Cand d = load_cand(G, raw, c);
+            const int ab = 3 * ti + rec_type(d.w);
+            const bool bonded = (d.w ^ wi) < 16;
+            const float r2o = cand_r2(d, raw, ho, qo, hf, h2), r2n = cand_r2(d, raw, hn, qn, hf, h2);
+            wca_m(md, r2o, ab, -1.f, a);
+            wca_m(md, r2n, ab, 1.f, a);
+            fene_m(md, r2o, ab, -1.f, bonded, a);
+            fene_m(md, r2n, ab, 1.f, bonded, a);
         }
     }
     return a;
 }
 
 __device__ __forceinline__ Acc32 inter_flip(const Group &G, const WarpScr &S, int nq, int lane, const ModelDev &md,
-                                            int kp, int kq, int wi, int tp, int tq)
+                                            bool raw, int kp, int kq, int cpad, int wi, int tp, int tq,
+                                            const HiLo &hp, const HiLo &hq, const Q3 &qp, const Q3 &qq, float hf,
+                                            float h2)
 {
     Acc32 a{0.f, 0.f, 0};
-    for (int e = lane; e < nq; e += 32) {
-        const int c = S.qc[e];
-        if (c == kp || c == kq) continue;
-        const int wj = G.sw[c];
-        const int tj = rec_type(wj);
-        const float rp = S.qr[e], rq = S.qr[QW + e];
-        // atom p: type tp -> tq; atom q: type tq -> tp
-        add_wca(md, rp, 3 * tp + tj, -1.f, a);
-        add_wca(md, rp, 3 * tq + tj, 1.f, a);
-        add_wca(md, rq, 3 * tq + tj, -1.f, a);
-        add_wca(md, rq, 3 * tp + tj, 1.f, a);
-        if ((wj ^ wi) < 16) {
-            add_fene(md, rp, 3 * tp + tj, -1.f, a);
-            add_fene(md, rp, 3 * tq + tj, 1.f, a);
-            add_fene(md, rq, 3 * tq + tj, -1.f, a);
-            add_fene(md, rq, 3 * tp + tj, 1.f, a);
-        }
-    }
-    return a;
-}
-
-__device__ __noinline__ Acc32 inter_mol(const Group &G, const WarpScr &S, int nq, int lane, const ModelDev &md,
-                                        const int *t3)
-{
-    Acc32 a{0.f, 0.f, 0};
-    for (int e = lane; e < nq; e += 32) {
-        const int c = S.qc[e];
-        const int tj = rec_type(G.sw[c]);
+    const int slots = nq > 32 ? 2 : 1;
 #pragma unroll
-        for (int s = 0; s < 3; ++s) {
-            const int ab = 3 * t3[s] + tj;
-            add_wca(md, S.qr[s * QW + e], ab, -1.f, a);
-            add_wca(md, S.qr[(3 + s) * QW + e], ab, 1.f, a);
+    for (int s = 0; s < 2; ++s) {
+        if (s < slots) {
+            const int c = queued(S, lane + 32 * s, nq, cpad, kp, kq);
+            const Cand d = load_cand(G, raw, c);
+            const int tj = rec_type(d.w);
+            const bool bonded = (d.w ^ wi) < 16;
+            const float rp = cand_r2(d, raw, hp, qp, hf, h2), rq = cand_r2(d, raw, hq, qq, hf, h2);
+            // atom p: type tp -> tq; atom q: type tq -> tp
+            wca_m(md, rp, 3 * tp + tj, -1.f, a);
+            wca_m(md, rp, 3 * tq + tj, 1.f, a);
+            wca_m(md, rq, 3 * tq + tj, -1.f, a);
+            wca_m(md, rq, 3 * tp + tj, 1.f, a);
+            fene_m(md, rp, 3 * tp + tj, -1.f, bonded, a);
+            fene_m(md, rp, 3 * tq + tj, 1.f, bonded, a);
+            fene_m(md, rq, 3 * tq + tj, -1.f, bonded, a);
+            fene_m(md, rq, 3 * tp + tj, 1.f, bonded, a);
         }
     }
     return a;
 }
 
-// intramolecular terms of a rotation (FP32, one lane)
-__device__ __noinline__ void rot_intra32(const ModelDev &md, const Q3 *qo, const Q3 *qn, const int *t3, float hf,
-                                         Acc32 &part)
+__device__ __noinline__ Acc32 inter_mol(const Group G, const WarpScr S, int nq, int lane, const ModelDev &md,
+                                        bool raw, const int *t3, const HiLo *ho, const HiLo *hn, const Q3 *qo,
+                                        const Q3 *qn, float hf, float h2)
+{
+    Acc32 a{0.f, 0.f, 0};
+    for (int s = 0; s < 2; ++s) {
+        const int e = lane + 32 * s;
+        if (e < nq) {
+            const Cand d = load_cand(G, raw, S.qc[e]);
+            const int tj = rec_type(d.w);
+            for (int m = 0; m < 3; ++m) {
+                const int ab = 3 * t3[m] + tj;
+                add_wca(md, cand_r2(d, raw, ho[m], qo[m], hf, h2), ab, -1.f, a);
+                add_wca(md, cand_r2(d, raw, hn[m], qn[m], hf, h2), ab, 1.f, a);
+            }
+        }
+    }
+    return a;
+}
+
+// intramolecular terms of a rotation (FP32, one lane), added to part
+__device__ __noinline__ Acc32 rot_intra32(const ModelDev &md, const Q3 *qo, const Q3 *qn, const int *t3, float hf,
+                                          Acc32 part)
 {
     const int pk3[3] = {0, 0, 1}, pl3[3] = {1, 2, 2};
     for (int pr = 0; pr < 3; ++pr) {
@@ -675,6 +808,7 @@ __device__ __noinline__ void rot_intra32(const ModelDev &md, const Q3 *qo, const
         add_fene(md, r2o, ab, -1.f, part);
         add_fene(md, r2n, ab, 1.f, part);
     }
+    return part;
 }
 
 // ---------------------------------------------------------------------------
@@ -685,29 +819,28 @@ struct CellCtx {
     const MixDev *mx;
     RecView rv;
     int K, n, cellL, nc;
-    bool small;
+    bool raw;               // n_c = 2: distances from the raw records
     uint32_t P[3];          // cell centre (fixed point): origin of the cell-local frame
     uint32_t shift[3];
-    uint64_t sweep, seed;
     double h, inv_h, T64;
-    float hf, rc2max, pre_r2, gap, T32;
+    float hf, h2f;          // h and h^2 in FP32
+    float pre_r2;           // screening radius squared (sigma units): 1.01 x the largest WCA cutoff squared
+    float r2q;              // the same in the units of the screens (fixed-point units squared unless raw)
+    float gap, T32;
     int32_t D_atom, D_mol;
     int *err;
 };
 
-__device__ __forceinline__ PosF local_of(const CellCtx &c, uint32_t x, uint32_t y, uint32_t z)
+__device__ __forceinline__ HiLo hilo_of(const CellCtx &c, const Q3 &q)
 {
-    PosF p;
-    p.x = (float)(int)(x - c.P[0]) * c.hf;
-    p.y = (float)(int)(y - c.P[1]) * c.hf;
-    p.z = (float)(int)(z - c.P[2]) * c.hf;
-    return p;
+    return make_hilo((int)(q.x - c.P[0]), (int)(q.y - c.P[1]), (int)(q.z - c.P[2]));
 }
 
 // Evaluate attempt `jr` of the current chunk (one warp, state read-only) and
-// leave its outcome in R (written by lane 0).
+// return its outcome (the same in every lane); with W > 1 lane 0 also leaves
+// in N what the conflict test of the later attempts of the round reads.
 template <int PREC, int W>
-__device__ void evaluate(const CellCtx &cx, const Group &G, const WarpScr &S, Res *R, int jr, int lane)
+__device__ Res evaluate(const CellCtx &cx, const Group &G, const WarpScr &S, Near *N, int jr, int lane)
 {
     const ModelDev &md = *cx.md;
     const uint32_t *w = G.rnd + 8 * jr;
@@ -719,11 +852,11 @@ __device__ void evaluate(const CellCtx &cx, const Group &G, const WarpScr &S, Re
     const int mvt = move_type(w[1], *cx.mx);
     int status = MC_ST_EVALUATED;
     int flags = 0, accept = 0;
-    float scale = 0.f;
-    double dE_log = 0.0, dE64 = __longlong_as_double(0x7FF8000000000000ll), used = 0.0;
+    float scale = 0.f, dE32 = 0.f;
+    double dE64 = __longlong_as_double(0x7FF8000000000000ll);
 
     int ks[3] = {k, -1, -1};
-    Q3 qo[3], qn[3];
+    Q3 qo[3] = {}, qn[3] = {};
     int t3o[3] = {0, 0, 0}, t3n[3] = {0, 0, 0};
     int nmv = 1;
     if (mvt == MC_MOVE_ATOM) {
@@ -736,7 +869,7 @@ __device__ void evaluate(const CellCtx &cx, const Group &G, const WarpScr &S, Re
         // the molecule's atoms in the own cell
         int k0 = -1, k1 = -1, k2 = -1;
         for (int j = 0; j < n; ++j) {
-            const int wj = G.rec[j].w;
+            const int wj = G.sw[j];
             if (rec_mol(wj) == mol) {
                 const int sl = rec_slot(wj);
                 if (sl == 0) k0 = j;
@@ -805,9 +938,16 @@ __device__ void evaluate(const CellCtx &cx, const Group &G, const WarpScr &S, Re
             }
         }
     }
+    // the moved atoms in the cell-local frame, old and new
+    HiLo ho[3], hn[3];
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+        ho[s] = hilo_of(cx, qo[s]);
+        hn[s] = hilo_of(cx, qn[s]);
+    }
 
     // the FP64 ordered sum of this move and its decision (-1: bond break)
-    auto exact = [&](double thr) {
+    auto exact = [&](double thr, int nq) {
         Move mv;
         mv.n = nmv;
         mv.mol = mol;
@@ -815,7 +955,7 @@ __device__ void evaluate(const CellCtx &cx, const Group &G, const WarpScr &S, Re
         mv.intra = mvt == MC_MOVE_MOL_ROT;
 #pragma unroll
         for (int s = 0; s < 3; ++s) {
-            mv.site[s] = s < nmv ? rec_site(G.rec[ks[s]].w) : -1;
+            mv.site[s] = s < nmv ? rec_site(G.sw[ks[s]]) : -1;
             mv.to[s] = t3o[s];
             mv.tn[s] = t3n[s];
             mv.qo[s][0] = qo[s].x;
@@ -826,59 +966,59 @@ __device__ void evaluate(const CellCtx &cx, const Group &G, const WarpScr &S, Re
             mv.qn[s][2] = qn[s].z;
         }
         double e64 = 0.0;
-        const int st = dE64_ordered(mv, cx.rv, S, K, md, cx.h, cx.hf, cx.pre_r2, lane, cx.err, e64);
+        const int st = dE64_ordered(mv, cx.rv, S, K, nq, md, cx.h, cx.hf, cx.pre_r2, lane, cx.err, e64);
         dE64 = e64;
         return (st == MC_ST_EVALUATED) ? ((e64 <= thr) ? 1 : 0) : -1;
     };
 
     if (status == MC_ST_EVALUATED) {
+        int qlen;
+        if (cx.raw) {
+            const Q3 pos[6] = {qo[0], qo[1], qo[2], qn[0], qn[1], qn[2]};
+            if (mvt == MC_MOVE_ATOM) {
+                const Q3 p2[2] = {qo[0], qn[0]};
+                qlen = screen_raw(G, S, K, lane, p2, 2, wi, false, cx.hf, cx.r2q);
+            } else if (mvt == MC_MOVE_FLIP) {
+                qlen = screen_raw(G, S, K, lane, pos, 2, wi, false, cx.hf, cx.r2q);
+            } else {
+                qlen = screen_raw(G, S, K, lane, pos, 6, wi, true, cx.hf, cx.r2q);
+            }
+        } else if (mvt == MC_MOVE_ATOM) {
+            qlen = screen_atom(G, S, K, lane, ho[0], hn[0], wi, cx.r2q);
+        } else if (mvt == MC_MOVE_FLIP) {
+            qlen = screen_flip(G, S, K, lane, ho[0], ho[1], wi, cx.r2q);
+        } else {
+            const HiLo a[3] = {ho[0], ho[1], ho[2]}, b[3] = {hn[0], hn[1], hn[2]};
+            qlen = screen_mol(G, S, K, lane, a, b, wi, cx.r2q);
+        }
+        __syncwarp();
+        const int nq = min(qlen, QW);
+        const int nq64 = qlen <= QW ? qlen : -1;   // overflowed queue: the FP64 sum scans every atom
+        const int cpad = (K + 1) & ~1;             // padding candidate (far, no molecule)
         if (PREC == MC_PREC_FP64) {
-            const int dec = exact(G.thr64[jr]);
+            const int dec = exact(G.thr64[jr], nq64);
             if (dec < 0) status = MC_ST_BOND_BREAK;
             accept = dec == 1;
-            dE_log = used = dE64;
         } else {
             const float thr32 = G.thr32[jr];
-            int qlen;
-            if (mvt == MC_MOVE_ATOM) {
-                const PosF so = PosF{G.sx[k], G.sy[k], G.sz[k]};
-                const PosF sn = local_of(cx, qn[0].x, qn[0].y, qn[0].z);
-                qlen = pass_atom(G, S, K, lane, cx.small, so, sn, wi, qo[0], qn[0], cx.hf, cx.rc2max);
-            } else if (mvt == MC_MOVE_FLIP) {
-                const PosF sp = PosF{G.sx[ks[0]], G.sy[ks[0]], G.sz[ks[0]]};
-                const PosF sq = PosF{G.sx[ks[1]], G.sy[ks[1]], G.sz[ks[1]]};
-                qlen = pass_flip(G, S, K, lane, cx.small, sp, sq, wi, qo[0], qo[1], cx.hf, cx.rc2max);
-            } else {
-                // copies: the helpers below take addresses, the hot path's registers stay registers
-                PosF so[3], sn[3];
-                const Q3 mo[3] = {qo[0], qo[1], qo[2]}, mn[3] = {qn[0], qn[1], qn[2]};
-#pragma unroll
-                for (int s = 0; s < 3; ++s) {
-                    so[s] = PosF{G.sx[ks[s]], G.sy[ks[s]], G.sz[ks[s]]};
-                    sn[s] = local_of(cx, qn[s].x, qn[s].y, qn[s].z);
-                }
-                qlen = pass_mol(G, S, K, lane, cx.small, so, sn, wi, mo, mn, cx.hf, cx.rc2max);
-            }
-            __syncwarp();
-            const int nq = min(qlen, QW);
             Acc32 part;
             if (mvt == MC_MOVE_ATOM) {
-                part = inter_atom(G, S, nq, lane, md, k, wi, t3o[0]);
+                part = inter_atom(G, S, nq, lane, md, cx.raw, k, cpad, wi, t3o[0], ho[0], hn[0], qo[0], qn[0], cx.hf,
+                                  cx.h2f);
             } else if (mvt == MC_MOVE_FLIP) {
-                part = inter_flip(G, S, nq, lane, md, ks[0], ks[1], wi, t3o[0], t3o[1]);
+                part = inter_flip(G, S, nq, lane, md, cx.raw, ks[0], ks[1], cpad, wi, t3o[0], t3o[1], ho[0], ho[1],
+                                  qo[0], qo[1], cx.hf, cx.h2f);
             } else {
                 const int tm[3] = {t3o[0], t3o[1], t3o[2]};
-                part = inter_mol(G, S, nq, lane, md, tm);
-                if (mvt == MC_MOVE_MOL_ROT && lane == 0) {
-                    const Q3 ro[3] = {qo[0], qo[1], qo[2]}, rn[3] = {qn[0], qn[1], qn[2]};
-                    rot_intra32(md, ro, rn, tm, cx.hf, part);
-                }
+                const HiLo a[3] = {ho[0], ho[1], ho[2]}, b[3] = {hn[0], hn[1], hn[2]};
+                const Q3 ro[3] = {qo[0], qo[1], qo[2]}, rn[3] = {qn[0], qn[1], qn[2]};
+                part = inter_mol(G, S, nq, lane, md, cx.raw, tm, a, b, ro, rn, cx.hf, cx.h2f);
+                if (mvt == MC_MOVE_MOL_ROT && lane == 0) part = rot_intra32(md, ro, rn, tm, cx.hf, part);
             }
             if (qlen > QW) part.guard = 1;
-            const float dE32 = warp_sum_f(part.dE);
+            dE32 = warp_sum_f(part.dE);
             const float mag = warp_sum_f(part.mag);
             const int guard = __any_sync(FULL, part.guard);
-            dE_log = used = (double)dE32;
             scale = mag;
             const float diff = fabsf(dE32 - thr32);
             const float marg = cx.gap * mag + 1e-6f * (cx.T32 + fabsf(thr32) + fabsf(dE32));
@@ -889,74 +1029,146 @@ __device__ void evaluate(const CellCtx &cx, const Group &G, const WarpScr &S, Re
                 const unsigned long long u52 = ((unsigned long long)w[2] << 20) | (unsigned long long)(w[3] >> 12);
                 const double u = __dmul_rn((double)(2ull * u52 + 1ull), 0x1p-53);
                 const double thr = -__dmul_rn(cx.T64, ln_series(u));
-                const int dec = exact(thr);
+                const int dec = exact(thr, nq64);
                 if (dec < 0) status = MC_ST_BOND_BREAK;
                 accept = dec == 1;
-                used = dE64;
             } else {
                 accept = dE32 <= thr32;
             }
         }
     }
 
-    if (lane == 0) {
-        R->status = status;
-        R->accept = accept;
-        R->flags = flags;
-        R->mvt = mvt;
-        R->nmv = nmv;
-        R->site = rec_site(wi);
-        R->mol = mol;
-        R->dE_used = used;
-        R->dE_log = dE_log;
-        R->dE64 = dE64;
-        R->scale = scale;
-        R->pairs = (mvt == MC_MOVE_MOL_TRANS || mvt == MC_MOVE_MOL_ROT) ? 6 : 2;
-        int na = 0;
-        for (int s = 0; s < 3; ++s) {
-            R->ks[s] = ks[s];
-            R->t3n[s] = t3n[s];
-            R->qn[s][0] = qn[s].x;
-            R->qn[s][1] = qn[s].y;
-            R->qn[s][2] = qn[s].z;
-        }
+    Res R;
+    R.status = status;
+    R.accept = accept;
+    R.flags = flags;
+    R.mvt = mvt;
+    R.nmv = nmv;
+    R.site = rec_site(wi);
+    R.mol = mol;
+    R.dE32 = dE32;
+    R.scale = scale;
+    R.dE64 = dE64;
+    R.pairs = (mvt == MC_MOVE_MOL_TRANS || mvt == MC_MOVE_MOL_ROT) ? 6 : 2;
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+        R.ks[s] = ks[s];
+        R.t3n[s] = t3n[s];
+        R.qn[s][0] = qn[s].x;
+        R.qn[s][1] = qn[s].y;
+        R.qn[s][2] = qn[s].z;
+        R.hn[s] = hn[s];
+    }
+    if (W > 1 && lane == 0) {
         // positions the move reads or writes, for the conflict test of the commit
-        // (one warp per cell: no later attempt of the round to protect)
-        if (W > 1 && status == MC_ST_EVALUATED) {
-            for (int s = 0; s < nmv; ++s) {
-                const PosF a = PosF{G.sx[ks[s]], G.sy[ks[s]], G.sz[ks[s]]};
-                R->px[na] = a.x; R->py[na] = a.y; R->pz[na] = a.z; ++na;
-                if (mvt != MC_MOVE_FLIP) {
-                    const PosF b = local_of(cx, qn[s].x, qn[s].y, qn[s].z);
-                    R->px[na] = b.x; R->py[na] = b.y; R->pz[na] = b.z; ++na;
+        int na = 0;
+        if (status == MC_ST_EVALUATED) {
+#pragma unroll
+            for (int s = 0; s < 3; ++s) {
+                if (s < nmv) {
+                    N->px[na] = ho[s].x; N->py[na] = ho[s].y; N->pz[na] = ho[s].z; ++na;
+                    if (mvt != MC_MOVE_FLIP) {
+                        N->px[na] = hn[s].x; N->py[na] = hn[s].y; N->pz[na] = hn[s].z; ++na;
+                    }
                 }
             }
         }
-        R->nat = na;
+        N->accept = accept;
+        N->mol = mol;
+        N->nat = na;
+    }
+    return R;
+}
+
+// Could an earlier accepted attempt of the round have changed the evaluation
+// of attempt wb?  Same molecule, or atoms within the conflict radius (1.01 x
+// the largest cutoff, fixed-point units squared).  One warp: the lanes take
+// the atom pairs of all earlier attempts at once (entries of attempts at or
+// after wb are read but masked); every lane returns the same answer.
+template <int W>
+__device__ __forceinline__ bool clashes(const Near *near, int wb, float rconf, int lane)
+{
+    const Near &B = near[wb];
+    bool hit = false;
+#pragma unroll
+    for (int wa = 0; wa < W - 1; ++wa) {
+        const Near &A = near[wa];
+        const bool live = (wa < wb) && A.accept != 0;
+        hit |= live && A.mol == B.mol;
+#pragma unroll
+        for (int m = 0; m < 2; ++m) {
+            const int p = min(lane + 32 * m, 35);         // atom pair (i, j); lanes past 35 repeat pair 35
+            const int i = p / 6, j = p - 6 * (p / 6);
+            const float dx = A.px[i] - B.px[j], dy = A.py[i] - B.py[j], dz = A.pz[i] - B.pz[j];
+            hit |= live && i < A.nat && j < B.nat && fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < rconf;
+        }
+    }
+    return __any_sync(FULL, hit);
+}
+
+// Apply attempt R (number `at` in the cell) to the staged state, count it, log
+// it.  One thread (lane 0 of the warp that evaluated it).
+template <int PREC>
+__device__ __forceinline__ void commit(const Group &G, const Res &R, int at, int K, Tally &t, const LogArgs &lg,
+                                       const RepInfo &ri, uint64_t sweep, int own_start)
+{
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {   // static indices keep the counts in registers
+        t.att[m] += R.mvt == m;
+        t.acc[m] += (R.mvt == m) & (R.accept != 0);
+    }
+    if (R.status == MC_ST_LEFT_CELL || R.status == MC_ST_NOT_IN_CELL) t.rej_geom += 1;
+    if (R.status == MC_ST_BOND_BREAK) t.rej_bond += 1;
+    if (R.status == MC_ST_EVALUATED || R.status == MC_ST_BOND_BREAK)
+        t.pairs += (unsigned long long)R.pairs * (unsigned long long)K;
+    t.rechecks += R.flags;
+    if (R.accept) {
+        // the running energy: FP64 sums in FP64 mode; in FP32 mode the few
+        // accepted Delta E of a cell are summed in FP32 (they carry FP32
+        // errors already) and the cell total joins the FP64 sum
+        if (PREC == MC_PREC_FP64) t.dE = __dadd_rn(t.dE, R.dE64);
+        else t.dEf += R.flags ? (float)R.dE64 : R.dE32;
+        if (R.mvt == MC_MOVE_FLIP) {
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                int4 rs = G.rec[R.ks[s]];
+                rs.w = (rs.w & ~3) | R.t3n[s];
+                G.rec[R.ks[s]] = rs;
+                G.sw[R.ks[s]] = rs.w;
+            }
+        } else {
+#pragma unroll
+            for (int s = 0; s < 3; ++s) {
+                if (s < R.nmv) {
+                    const int ks = R.ks[s];
+                    int4 rs = G.rec[ks];
+                    rs.x = (int)R.qn[s][0];
+                    rs.y = (int)R.qn[s][1];
+                    rs.z = (int)R.qn[s][2];
+                    G.rec[ks] = rs;
+                    G.sx[ks] = R.hn[s].x;
+                    G.sy[ks] = R.hn[s].y;
+                    G.sz[ks] = R.hn[s].z;
+                    G.sl[ks] = R.hn[s].lo;
+                }
+            }
+        }
+    }
+    if (lg.base != nullptr) {
+        const uint64_t sl = sweep - lg.sweep0;
+        mc_log_entry *e = lg.base + (size_t)ri.site_off * (size_t)lg.n_sweeps + (size_t)sl * (size_t)ri.n_sites +
+                          (size_t)(own_start - ri.site_off) + (size_t)at;
+        e->site = R.site;
+        e->move = (int16_t)R.mvt;
+        e->flags = (int16_t)R.flags;
+        e->status = R.status;
+        e->accepted = R.accept;
+        const double dE_mode = PREC == MC_PREC_FP64 ? R.dE64 : (double)R.dE32;
+        e->dE = R.status == MC_ST_EVALUATED ? dE_mode : __longlong_as_double(0x7FF8000000000000ll);
+        e->dE64 = R.dE64;
+        e->scale = (double)R.scale;
     }
 }
-
-// Could accepted move A (committed earlier in the round) have changed the
-// evaluation of B?  Same molecule, or atoms within 1.01 x the largest cutoff.
-__device__ __forceinline__ bool conflicts(const Res &A, const Res &B, float rconf2)
-{
-    if (A.mol == B.mol) return true;
-    for (int i = 0; i < A.nat; ++i)
-        for (int j = 0; j < B.nat; ++j) {
-            const float dx = A.px[i] - B.px[j], dy = A.py[i] - B.py[j], dz = A.pz[i] - B.pz[j];
-            if (dx * dx + dy * dy + dz * dz < rconf2) return true;
-        }
-    return false;
-}
-
-// ---------------------------------------------------------------------------
-// The phase kernel
-// ---------------------------------------------------------------------------
-struct Tally {
-    unsigned att[4], acc[4], rej_geom, rej_bond, rechecks;
-    unsigned long long pairs;
-    double dE_cell;
-};
 
 // copy the model tables and move mix into the block's shared memory
 __device__ __forceinline__ void load_tables(const DevState &d, ModelDev &md, MixDev &mx)
@@ -996,15 +1208,15 @@ __device__ void run_cell(const DevState &d, int buf, int colour, const LogArgs &
     const int cz = 2 * (a_loc / (h2 * h2)) + ((colour >> 2) & 1);
     const int cellL = (cz * nc + cy) * nc + cx;
     const int cellG = ri.cell_off + cellL;
-    const bool small = nc == 2;
-    const int ns = small ? 8 : 27;
+    const bool raw = nc == 2;
+    const int ns = raw ? 8 : 27;
 
     // ---- neighbourhood: own cell first ----
     if (wig == 0) {
         int cnt = 0, cst = 0;
         if (lane < ns) {
             int ox, oy, oz;
-            if (small) {
+            if (raw) {
                 ox = lane & 1; oy = (lane >> 1) & 1; oz = lane >> 2;
             } else {
                 const int kk = (lane == 0) ? 13 : (lane <= 13 ? lane - 1 : lane);   // 13 = (0,0,0)
@@ -1038,7 +1250,7 @@ __device__ void run_cell(const DevState &d, int buf, int colour, const LogArgs &
     const int K = G.misc[MS_K];
     const int n = G.misc[MS_N];
     const int own_start = G.misc[MS_START];
-    if (K + 1 > cap || n > rec_cap) {
+    if (K + PADS > cap || n > rec_cap) {
         if (gt == 0) {
             atomicOr(d.err, ERR_STENCIL);
             d.cell_dE[cellG] = 0.0;
@@ -1053,28 +1265,28 @@ __device__ void run_cell(const DevState &d, int buf, int colour, const LogArgs &
     c.n = n;
     c.cellL = cellL;
     c.nc = nc;
-    c.small = small;
+    c.raw = raw;
     c.shift[0] = ct.shift[0];
     c.shift[1] = ct.shift[1];
     c.shift[2] = ct.shift[2];
     c.P[0] = (uint32_t)(((uint64_t)(2 * cx + 1) << 32) / (uint64_t)(2 * nc)) - ct.shift[0];
     c.P[1] = (uint32_t)(((uint64_t)(2 * cy + 1) << 32) / (uint64_t)(2 * nc)) - ct.shift[1];
     c.P[2] = (uint32_t)(((uint64_t)(2 * cz + 1) << 32) / (uint64_t)(2 * nc)) - ct.shift[2];
-    c.sweep = ct.sweep;
-    c.seed = dy.seed;
     c.h = ri.h;
     c.inv_h = ri.inv_h;
     c.hf = ri.hf;
+    c.h2f = ri.h2f;
     c.T64 = dy.T;
-    c.T32 = (float)dy.T;
+    c.T32 = dy.T32;
     c.D_atom = dy.D_atom;
     c.D_mol = dy.D_mol;
     c.gap = md.recheck_gap_f;
     c.err = d.err;
     float rc2max = 0.f;
     for (int kk = 0; kk < 9; ++kk) rc2max = fmaxf(rc2max, md.rc2f[kk]);
-    c.rc2max = rc2max;
     c.pre_r2 = rc2max * 1.01f;
+    c.r2q = raw ? c.pre_r2 : c.pre_r2 / c.h2f;
+    const float rconf = rc2max * 1.0201f / c.h2f;   // (1.01 rc)^2, fixed-point units
     c.rv.smem = G.rec;
     c.rv.full = d.full_rec != 0;
     c.rv.n = n;
@@ -1082,21 +1294,32 @@ __device__ void run_cell(const DevState &d, int buf, int colour, const LogArgs &
     c.rv.cstart = G.cstart;
     c.rv.coff = G.coff;
     c.rv.ns = ns;
-    const float rconf2 = rc2max * 1.0201f;   // (1.01 rc)^2
 
-    // ---- stage: issue all loads of a thread before using any ----
+    // ---- stage: issue every load of a thread (records, and the random words of
+    // the first 32 attempts) before using any ----
     {
         const int4 *src = d.rec[buf];
+        const int a = gt;
+        const bool has_rnd = gt < 32 && gt < n;
+        uint4 rb0 = make_uint4(0, 0, 0, 0), rb1 = rb0;
+        double th64 = 0.0;
+        float th32 = 0.f;
+        if (has_rnd) {
+            const size_t slot = (size_t)own_start + (size_t)a;
+            rb0 = d.att_rnd[2 * slot];
+            rb1 = d.att_rnd[2 * slot + 1];
+            if (PREC == MC_PREC_FP64) th64 = d.att_thr64[slot];
+            else th32 = d.att_thr32[slot];
+        }
         constexpr int UNR = 4;
-        int kk = 0;   // neighbour cell of the current index (indices only grow)
         for (int base = gt; base < K; base += UNR * T) {
             int4 rc[UNR];
 #pragma unroll
             for (int u = 0; u < UNR; ++u) {
                 const int idx = base + u * T;
                 if (idx < K) {
-                    while (G.coff[kk + 1] <= idx) ++kk;
-                    rc[u] = src[G.cstart[kk] + (idx - G.coff[kk])];
+                    const int s = find_segment(G.coff, ns, idx);
+                    rc[u] = src[G.cstart[s] + (idx - G.coff[s])];
                 }
             }
 #pragma unroll
@@ -1104,116 +1327,84 @@ __device__ void run_cell(const DevState &d, int buf, int colour, const LogArgs &
                 const int idx = base + u * T;
                 if (idx < K) {
                     if (idx < rec_cap) G.rec[idx] = rc[u];
+                    if (idx < n) G.orig[idx] = rc[u];
                     G.sw[idx] = rc[u].w;
-                    const PosF p = local_of(c, (uint32_t)rc[u].x, (uint32_t)rc[u].y, (uint32_t)rc[u].z);
-                    G.sx[idx] = p.x;
-                    G.sy[idx] = p.y;
-                    G.sz[idx] = p.z;
+                    const HiLo hl = hilo_of(c, Q3{(uint32_t)rc[u].x, (uint32_t)rc[u].y, (uint32_t)rc[u].z});
+                    G.sx[idx] = hl.x;
+                    G.sy[idx] = hl.y;
+                    G.sz[idx] = hl.z;
+                    G.sl[idx] = hl.lo;
                 }
             }
         }
-        if (gt == 0) {
-            // padding partner for the odd last pair: far away, no molecule
-            G.sx[K] = FAR;
-            G.sy[K] = FAR;
-            G.sz[K] = FAR;
-            G.sw[K] = 0x7FFFFFFF;
-            if (K < rec_cap) G.rec[K] = make_int4(0, 0, 0, 0x7FFFFFFF);
+        if (has_rnd) {
+            uint4 *wv = (uint4 *)(G.rnd + 8 * a);
+            wv[0] = rb0;
+            wv[1] = rb1;
+            if (PREC == MC_PREC_FP64) G.thr64[a] = th64;
+            else G.thr32[a] = th32;
+        }
+        if (gt < PADS) {
+            // padding candidates: far away, no molecule (the screens and the
+            // interaction passes read them instead of branching)
+            const int i = K + gt;
+            G.sx[i] = FAR;
+            G.sy[i] = FAR;
+            G.sz[i] = FAR;
+            G.sl[i] = 0;
+            G.sw[i] = PAD_W;
+            if (i < rec_cap) G.rec[i] = make_int4(0, 0, 0, PAD_W);
         }
     }
     gsync<W>(gid);
 
     Tally t{};
     for (int a0 = 0; a0 < n; a0 += 32) {
-        if (wig == 0) {
-            // random words and thresholds drawn by the cell-list build, one slot per attempt
-            const int a = a0 + lane;
-            if (a < n) {
-                const size_t slot = (size_t)own_start + (size_t)a;
-                const uint4 b0 = d.att_rnd[2 * slot], b1 = d.att_rnd[2 * slot + 1];
-                uint4 *w = (uint4 *)(G.rnd + 8 * lane);
-                w[0] = b0;
-                w[1] = b1;
-                if (PREC == MC_PREC_FP64) G.thr64[lane] = d.att_thr64[slot];
-                else G.thr32[lane] = d.att_thr32[slot];
+        if (a0 > 0) {
+            // random words and thresholds of the next chunk (cells with more than 32 atoms)
+            if (wig == 0) {
+                const int a = a0 + lane;
+                if (a < n) {
+                    const size_t slot = (size_t)own_start + (size_t)a;
+                    uint4 *wv = (uint4 *)(G.rnd + 8 * lane);
+                    wv[0] = d.att_rnd[2 * slot];
+                    wv[1] = d.att_rnd[2 * slot + 1];
+                    if (PREC == MC_PREC_FP64) G.thr64[lane] = d.att_thr64[slot];
+                    else G.thr32[lane] = d.att_thr32[slot];
+                }
             }
+            gsync<W>(gid);
         }
-        gsync<W>(gid);
         const int a_end = min(n, a0 + 32);
         int a = a0;
         while (a < a_end) {
-            // evaluate attempts a .. a+W-1, one per warp, on the same state
-            if (a + wig < a_end) evaluate<PREC, W>(c, G, S, G.res + wig, a + wig - a0, lane);
-            gsync<W>(gid);
-            if (gt == 0) {
-                // commit in order, up to the first attempt an earlier accepted one may have changed
-                const int nw = min(W, a_end - a);
-                int adv = 0;
-                for (int wj = 0; wj < nw; ++wj) {
-                    const Res &R = G.res[wj];
-                    if (W > 1) {
-                        bool clash = false;
-                        for (int wa = 0; wa < wj && !clash; ++wa)
-                            if (G.res[wa].accept) clash = conflicts(G.res[wa], R, rconf2);
-                        if (clash) break;
-                    }
-                    const int at = a + wj;
-                    t.att[R.mvt] += 1;
-                    if (R.status == MC_ST_LEFT_CELL || R.status == MC_ST_NOT_IN_CELL) t.rej_geom += 1;
-                    if (R.status == MC_ST_BOND_BREAK) t.rej_bond += 1;
-                    if (R.status == MC_ST_EVALUATED || R.status == MC_ST_BOND_BREAK)
-                        t.pairs += (unsigned long long)R.pairs * (unsigned long long)K;
-                    t.rechecks += R.flags;
-                    if (R.accept) {
-                        t.acc[R.mvt] += 1;
-                        t.dE_cell = __dadd_rn(t.dE_cell, R.dE_used);
-                        if (R.mvt == MC_MOVE_FLIP) {
-                            for (int s = 0; s < 2; ++s) {
-                                int4 rs = G.rec[R.ks[s]];
-                                rs.w = (rs.w & ~3) | R.t3n[s];
-                                G.rec[R.ks[s]] = rs;
-                                G.sw[R.ks[s]] = rs.w;
-                            }
-                        } else {
-                            for (int s = 0; s < R.nmv; ++s) {
-                                int4 rs = G.rec[R.ks[s]];
-                                rs.x = (int)R.qn[s][0];
-                                rs.y = (int)R.qn[s][1];
-                                rs.z = (int)R.qn[s][2];
-                                G.rec[R.ks[s]] = rs;
-                                const PosF p = local_of(c, R.qn[s][0], R.qn[s][1], R.qn[s][2]);
-                                G.sx[R.ks[s]] = p.x;
-                                G.sy[R.ks[s]] = p.y;
-                                G.sz[R.ks[s]] = p.z;
-                            }
-                        }
-                    }
-                    if (lg.base != nullptr) {
-                        const uint64_t sl = ct.sweep - lg.sweep0;
-                        mc_log_entry *e = lg.base + (size_t)ri.site_off * (size_t)lg.n_sweeps +
-                                          (size_t)sl * (size_t)ri.n_sites + (size_t)(own_start - ri.site_off) +
-                                          (size_t)at;
-                        e->site = R.site;
-                        e->move = (int16_t)R.mvt;
-                        e->flags = (int16_t)R.flags;
-                        e->status = R.status;
-                        e->accepted = R.accept;
-                        e->dE = R.status == MC_ST_EVALUATED ? R.dE_log : __longlong_as_double(0x7FF8000000000000ll);
-                        e->dE64 = R.dE64;
-                        e->scale = (double)R.scale;
-                    }
-                    ++adv;
+            // evaluate attempts a .. a+nw-1, one per warp, on the same state
+            const int nw = min(W, a_end - a);
+            Res R;
+            if (wig < nw) R = evaluate<PREC, W>(c, G, S, G.near + wig, a + wig - a0, lane);
+            int adv = 1;
+            if constexpr (W > 1) {
+                gsync<W>(gid);
+                // commit in order up to the first attempt an earlier accepted one may have changed
+                if (wig < nw) {
+                    const bool cl = clashes<W>(G.near, wig, rconf, lane);
+                    if (lane == 0) G.misc[MS_CLASH + wig] = cl;
                 }
-                if (W > 1) G.misc[MS_ADV] = adv;
-            }
-            if constexpr (W == 1) {
-                __syncwarp();
-                a += 1;
+                gsync<W>(gid);
+                adv = nw;
+                for (int j = 1; j < nw; ++j)
+                    if (G.misc[MS_CLASH + j]) {
+                        adv = j;
+                        break;
+                    }
             } else {
-                gsync<W>(gid);
-                a += G.misc[MS_ADV];
-                gsync<W>(gid);
+                __syncwarp();
             }
+            // committed attempts touch different molecules: each warp applies its own
+            if (wig < adv && lane == 0) commit<PREC>(G, R, a + wig, K, t, lg, ri, ct.sweep, own_start);
+            if constexpr (W > 1) gsync<W>(gid);
+            else __syncwarp();
+            a += adv;
         }
     }
 
@@ -1221,7 +1412,7 @@ __device__ void run_cell(const DevState &d, int buf, int colour, const LogArgs &
     int4 *dst = d.rec[buf] + own_start;
     for (int kk = gt; kk < n; kk += T) {
         const int4 nw = G.rec[kk];
-        const int4 od = dst[kk];
+        const int4 od = G.orig[kk];
         const int site = ri.site_off + rec_site(nw.w);
         const uint32_t o3[3] = {(uint32_t)od.x, (uint32_t)od.y, (uint32_t)od.z};
         const uint32_t n3[3] = {(uint32_t)nw.x, (uint32_t)nw.y, (uint32_t)nw.z};
@@ -1233,8 +1424,27 @@ __device__ void run_cell(const DevState &d, int buf, int colour, const LogArgs &
         }
         dst[kk] = nw;
     }
+    // ---- counts: the warps' tallies in warp order ----
+    if constexpr (W > 1) {
+        if (lane == 0) G.tally[wig] = t;
+        gsync<W>(gid);
+        if (gt == 0)
+            for (int j = 1; j < W; ++j) {
+                const Tally &u = G.tally[j];
+                for (int m = 0; m < 4; ++m) {
+                    t.att[m] += u.att[m];
+                    t.acc[m] += u.acc[m];
+                }
+                t.rej_geom += u.rej_geom;
+                t.rej_bond += u.rej_bond;
+                t.rechecks += u.rechecks;
+                t.pairs += u.pairs;
+                if (PREC == MC_PREC_FP64) t.dE = __dadd_rn(t.dE, u.dE);
+                else t.dEf += u.dEf;
+            }
+    }
     if (gt == 0) {
-        d.cell_dE[cellG] = t.dE_cell;
+        d.cell_dE[cellG] = PREC == MC_PREC_FP64 ? t.dE : (double)t.dEf;
         unsigned long long *st = d.stats + (size_t)r * STAT_N;
         for (int m = 0; m < 4; ++m) {
             if (t.att[m]) atomicAdd(st + STAT_ATT + m, (unsigned long long)t.att[m]);
@@ -1248,8 +1458,9 @@ __device__ void run_cell(const DevState &d, int buf, int colour, const LogArgs &
 }
 
 // One colour phase, one launch: group g of the grid owns active cell g.
+// W = 1 serves large grids (many cells per SM): registers for three resident blocks
 template <int PREC, int W>
-__global__ void __launch_bounds__(BLOCK) phase_kernel(DevState d, int buf, int colour, LogArgs lg)
+__global__ void __launch_bounds__(BLOCK, W == 1 ? 3 : 1) phase_kernel(DevState d, int buf, int colour, LogArgs lg)
 {
     constexpr int CPB = BLOCK / (32 * W);
     extern __shared__ __align__(16) unsigned char smem[];
@@ -1296,38 +1507,35 @@ __global__ void __launch_bounds__(BLOCK) finalize_kernel(DevState d)
 // ---------------------------------------------------------------------------
 // Persistent sweeps: one cooperative launch runs n_sweeps whole sweeps (cell
 // list, 8 colour phases, finalisation), the stages separated by a grid-wide
-// barrier.  Every wait of the barrier is bounded: after about a second it
+// barrier.  Every wait of the barrier is bounded: after a few seconds it
 // records ERR_TIMEOUT and the kernel leaves, instead of waiting forever.
 // ---------------------------------------------------------------------------
 struct GridBar {
-    unsigned int *count;
-    unsigned int *gen;
-    int *scan_tot;       // one per block: cell-count total of the block's chunk
+    unsigned int *count;  // arrivals since the launch began (zero at launch)
+    int *scan_tot;        // one per block: cell-count total of the block's chunk
 };
 
-__device__ bool grid_sync(const GridBar &gb, int *err)
+// Arrive, then wait until every block has arrived as often as this one.  The
+// count only grows, so no reset is needed between barriers; `target` is the
+// caller's running total (thread 0 only).  The wait is bounded.
+__device__ bool grid_sync(const GridBar &gb, unsigned int &target, int *err)
 {
     __shared__ int ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         ok = 1;
-        volatile unsigned int *vgen = gb.gen;
-        const unsigned int g0 = *vgen;
+        target += gridDim.x;
         __threadfence();
-        const unsigned int arrived = atomicAdd(gb.count, 1u);
-        if (arrived == gridDim.x - 1) {
-            atomicExch(gb.count, 0u);
-            __threadfence();
-            atomicAdd(gb.gen, 1u);
-        } else {
-            unsigned long long spins = 0;
-            while (*vgen == g0) {
-                if (++spins > (1ull << 24)) {
-                    atomicOr(err, ERR_TIMEOUT);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(64);
+        atomicAdd(gb.count, 1u);
+        unsigned long long spins = 0;
+        for (;;) {
+            unsigned int v;
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(gb.count) : "memory");
+            if ((int)(v - target) >= 0) break;
+            if (++spins > (1ull << 23)) {
+                atomicOr(err, ERR_TIMEOUT);
+                ok = 0;
+                break;
             }
         }
         __threadfence();
@@ -1359,7 +1567,7 @@ __device__ __forceinline__ int block_excl_scan(int v, int *tmp, int &total)
 }
 
 template <int PREC, int W>
-__global__ void __launch_bounds__(BLOCK) sweep_persistent(DevState d, int buf0, int n_sweeps, GridBar gb)
+__global__ void __launch_bounds__(BLOCK, W == 1 ? 3 : 1) sweep_persistent(DevState d, int buf0, int n_sweeps, GridBar gb)
 {
     constexpr int T = 32 * W;
     constexpr int CPB = BLOCK / T;
@@ -1381,10 +1589,11 @@ __global__ void __launch_bounds__(BLOCK) sweep_persistent(DevState d, int buf0, 
     const int chunk = (nC + gridDim.x - 1) / gridDim.x;
     const int lo = min(nC, (int)blockIdx.x * chunk), hi = min(nC, lo + chunk);
     int buf = buf0;
+    unsigned int bar_target = 0;
     for (int s = 0; s < n_sweeps; ++s) {
         // ---- cell list: count (cell_count is zero on entry) ----
         for (int g = tid; g < d.n_sites; g += nthr) cl_count_item(d, buf, g);
-        if (!grid_sync(gb, d.err)) return;
+        if (!grid_sync(gb, bar_target, d.err)) return;
         // ---- exclusive scan: chunk totals, then each block scans its chunk ----
         {
             int sum = 0;
@@ -1393,7 +1602,7 @@ __global__ void __launch_bounds__(BLOCK) sweep_persistent(DevState d, int buf0, 
             block_excl_scan(sum, tmp, total);
             if (threadIdx.x == 0) gb.scan_tot[blockIdx.x] = total;
         }
-        if (!grid_sync(gb, d.err)) return;
+        if (!grid_sync(gb, bar_target, d.err)) return;
         {
             int off = 0, all = 0;
             for (int b = threadIdx.x; b < (int)gridDim.x; b += BLOCK) {
@@ -1415,23 +1624,23 @@ __global__ void __launch_bounds__(BLOCK) sweep_persistent(DevState d, int buf0, 
             }
             if (blockIdx.x == 0 && threadIdx.x == 0) d.cell_start[nC] = t2;
         }
-        if (!grid_sync(gb, d.err)) return;
+        if (!grid_sync(gb, bar_target, d.err)) return;
         // ---- scatter, then order each cell and draw its attempts' random numbers ----
         for (int g = tid; g < d.n_sites; g += nthr) cl_scatter_item(d, buf, buf ^ 1, g);
-        if (!grid_sync(gb, d.err)) return;
+        if (!grid_sync(gb, bar_target, d.err)) return;
         for (int c = blockIdx.x * (BLOCK / 32) + warp; c < nC; c += gridDim.x * (BLOCK / 32))
             cl_order_cell(d, buf ^ 1, c, lane);
-        if (!grid_sync(gb, d.err)) return;
+        if (!grid_sync(gb, bar_target, d.err)) return;
         // ---- the 8 colours ----
         for (int colour = 0; colour < 8; ++colour) {
             for (int g = blockIdx.x * CPB + gid; g < d.n_act; g += gridDim.x * CPB)
                 run_cell<PREC, W>(d, buf ^ 1, colour, none, g, md, mx, gsmem, gid);
-            if (!grid_sync(gb, d.err)) return;
+            if (!grid_sync(gb, bar_target, d.err)) return;
         }
         // ---- finalise the sweep; clear the counts for the next one ----
         for (int r = blockIdx.x; r < d.n_rep; r += gridDim.x) finalize_replica(d, r, red);
         for (int c = tid; c < nC; c += nthr) d.cell_count[c] = 0;
-        if (!grid_sync(gb, d.err)) return;
+        if (!grid_sync(gb, bar_target, d.err)) return;
         buf ^= 1;
     }
 }
@@ -1533,8 +1742,10 @@ int persistent_grid(const DevState &d, int warps_per_cell, int max_blocks)
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_kernel(d.precision, warps_per_cell), BLOCK,
                                                       sm) != cudaSuccess)
         return 0;
+    // one block per group of active cells: blocks without a cell would only
+    // add arrivals to every grid barrier
     const int cpb = BLOCK / (32 * warps_per_cell);
-    const int needed = std::max((d.n_act + cpb - 1) / cpb, sms);
+    const int needed = std::max((d.n_act + cpb - 1) / cpb, 32);
     return std::max(0, std::min(std::min(per_sm * sms, needed), max_blocks));
 }
 
@@ -1543,7 +1754,7 @@ int launch_persistent(const DevState &d, int buf, int n_sweeps, int warps_per_ce
 {
     const int rec_cap = d.full_rec ? d.stencil_cap : d.own_cap;
     const size_t sm = phase_smem_bytes(d.stencil_cap, rec_cap, warps_per_cell);
-    GridBar gb{bar, bar + 1, scan_tot};
+    GridBar gb{bar, scan_tot};
     DevState dd = d;
     void *args[] = {(void *)&dd, (void *)&buf, (void *)&n_sweeps, (void *)&gb};
     const cudaError_t e = cudaLaunchCooperativeKernel(persistent_kernel(d.precision, warps_per_cell), dim3(grid),
