@@ -70,7 +70,6 @@ struct mc_handle {
     int n_cells = 0;
     int n_act = 0;
     int stencil_cap = 0;
-    int full_rec = 1;
     int own_cap = 0;
     size_t smem_bytes = 0;
     int pgrid = 0;                       // blocks of the persistent sweep (0: CUDA graphs instead)
@@ -419,7 +418,6 @@ int create_impl(mc_handle **out, int n_rep, const double *L, const int32_t *n_mo
     // layout
     long long sites = 0, cells = 0, act = 0;
     double max_stencil = 0.0, max_own = 0.0;
-    bool any_small = false;
     std::vector<int> act_off(n_rep + 1, 0), rep_of_site;
     for (int r = 0; r < n_rep; ++r) {
         if (n_mol[r] < 1 || n_mol[r] > kMaxMolecules) {
@@ -468,7 +466,6 @@ int create_impl(mc_handle **out, int n_rep, const double *L, const int32_t *n_mo
         max_stencil = std::max(max_stencil, std::min(st, (double)ri.n_sites));
         const double own = (nc == 2) ? (double)ri.n_sites : per_cell + 6.0 * std::sqrt(per_cell) + 16.0;
         max_own = std::max(max_own, std::min(own, (double)ri.n_sites));
-        any_small = any_small || nc == 2;
         if (sites > (1LL << 30)) {
             delete h;
             return fail(MC_ERR_INVALID_ARG, "too many sites");
@@ -488,11 +485,8 @@ int create_impl(mc_handle **out, int n_rep, const double *L, const int32_t *n_mo
     }
     if (o.warps_per_cell > 0) h->wpb = o.warps_per_cell;
     else h->wpb = h->n_act >= 152 * 12 ? 1 : (h->n_act >= 152 * 3 ? 2 : 4);
-    // raw records of the whole neighbourhood in shared memory when every
-    // attempt needs them (FP64 mode; n_c = 2 boxes), else of the own cell only
-    h->full_rec = (h->precision == MC_PREC_FP64 || any_small) ? 1 : 0;
-    h->own_cap = h->full_rec ? cap : std::max(32, ((int)std::ceil(max_own) + 15) / 16 * 16);
-    h->smem_bytes = phase_smem_bytes(cap, h->full_rec ? cap : h->own_cap, h->wpb);
+    h->own_cap = std::min(cap, std::max(32, ((int)std::ceil(max_own) + 15) / 16 * 16));
+    h->smem_bytes = phase_smem_bytes(cap, h->own_cap, h->wpb);
     if (h->smem_bytes > 220u * 1024u) {
         delete h;
         return fail(MC_ERR_INVALID_ARG, "stencil capacity too large for shared memory");
@@ -515,7 +509,6 @@ int create_impl(mc_handle **out, int n_rep, const double *L, const int32_t *n_mo
     d.n_cells = h->n_cells;
     d.n_act = h->n_act;
     d.stencil_cap = cap;
-    d.full_rec = h->full_rec;
     d.own_cap = h->own_cap;
     d.precision = h->precision;
     const int M_tot = h->n_sites / 3;

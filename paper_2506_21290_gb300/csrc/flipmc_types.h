@@ -86,9 +86,8 @@ struct DevState {
     int n_sites;         // total over replicas
     int n_cells;         // total over replicas
     int n_act;           // active cells per colour, total over replicas
-    int stencil_cap;     // atoms staged per neighbourhood (plus one padding slot)
-    int full_rec;        // 1: stage raw records of the whole neighbourhood; 0: own cell only
-    int own_cap;         // raw records staged when full_rec == 0
+    int stencil_cap;     // atoms staged per neighbourhood (plus kPadSlots padding candidates)
+    int own_cap;         // atoms of the own cell a neighbourhood may hold
     int precision;
     const RepInfo *rep;
     const RepParam *par;

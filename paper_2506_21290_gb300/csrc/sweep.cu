@@ -149,6 +149,44 @@ __device__ __forceinline__ float r2_int32f(const int4 &r, const Q3 b, float hf)
 // shared memory
 // ---------------------------------------------------------------------------
 
+// ---------------------------------------------------------------------------
+// Bulk copies global -> shared (cp.async.bulk) completing on an mbarrier
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *mb)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n\tfence.proxy.async.shared::cta;" ::"r"(smem_u32(mb))
+                 : "memory");
+}
+
+// the one arrival of a phase, announcing the bytes its copies will deliver
+__device__ __forceinline__ void mbar_arrive_expect(uint64_t *mb, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mb)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_done(uint64_t *mb, unsigned parity)
+{
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok)
+                 : "r"(smem_u32(mb)), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+
+// bytes (a multiple of 16, both addresses 16-byte aligned) from global to shared
+__device__ __forceinline__ void bulk_to_smem(void *dst, const void *src, unsigned bytes, uint64_t *mb)
+{
+    asm volatile("fence.proxy.async;\n\t"
+                 "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(mb))
+                 : "memory");
+}
+
 // per warp: interaction queue, and (aliased, used after it) the FP64 term buffers
 struct WarpScr {
     int *qc;                    // [QW + 1] queued candidate indices, then a slot that takes discarded writes
@@ -189,8 +227,9 @@ struct Group {
     float *sx, *sy, *sz;        // [cap] H of the staged atoms (fixed-point units)
     int *sl;                    // [cap] their packed low bytes
     int *sw;                    // [cap] record words
-    int4 *rec;                  // [rec_cap] raw records {qx, qy, qz, w}, own cell first
-    int4 *orig;                 // [rec_cap] the own cell as staged (periodic images at write-back)
+    int4 *rec;                  // [cap] raw records {qx, qy, qz, w} of the neighbourhood, own cell first
+    int4 *orig;                 // [own_cap] the own cell as staged (periodic images at write-back)
+    uint64_t *mbar;             // completion barrier of the bulk copies that stage rec
     uint32_t *rnd;              // [32 * 8] random words of a chunk of attempts
     double *thr64;              // [32]
     float *thr32;               // [32]
@@ -202,7 +241,7 @@ struct Group {
     unsigned char *warp_base;   // W per-warp scratch blocks
 };
 
-enum { MS_K = 0, MS_N = 1, MS_START = 2, MS_CLASH = 4 };
+enum { MS_K = 0, MS_N = 1, MS_START = 2, MS_PHASE = 3, MS_CLASH = 4, MS_FAIL = 8 };
 
 __host__ __device__ constexpr size_t al16(size_t x) { return (x + 15) & ~size_t(15); }
 
@@ -213,14 +252,15 @@ __host__ __device__ inline size_t warp_scr_bytes()
     return (q > k ? q : k) + 2 * al16(sizeof(double) * TERM_CAP) + al16(sizeof(int) * 4);
 }
 
-__host__ __device__ inline size_t group_bytes(int cap, int rec_cap, int W)
+__host__ __device__ inline size_t group_bytes(int cap, int own_cap, int W)
 {
-    return 5 * al16(sizeof(float) * cap) + 2 * al16(sizeof(int4) * rec_cap) + al16(sizeof(uint32_t) * 256) +
+    return 5 * al16(sizeof(float) * cap) + al16(sizeof(int4) * cap) + al16(sizeof(int4) * own_cap) + 16 +
+           al16(sizeof(uint32_t) * 256) +
            al16(sizeof(double) * 32) + al16(sizeof(float) * 32) + 3 * al16(sizeof(int) * 32) +
            al16(sizeof(Near) * W) + al16(sizeof(Tally) * W) + (size_t)W * warp_scr_bytes();
 }
 
-__device__ inline Group carve(unsigned char *base, int cap, int rec_cap, int W)
+__device__ inline Group carve(unsigned char *base, int cap, int own_cap, int W)
 {
     Group s;
     size_t o = 0;
@@ -234,8 +274,9 @@ __device__ inline Group carve(unsigned char *base, int cap, int rec_cap, int W)
     s.sz = (float *)take(sizeof(float) * cap);
     s.sl = (int *)take(sizeof(int) * cap);
     s.sw = (int *)take(sizeof(int) * cap);
-    s.rec = (int4 *)take(sizeof(int4) * rec_cap);
-    s.orig = (int4 *)take(sizeof(int4) * rec_cap);
+    s.rec = (int4 *)take(sizeof(int4) * cap);
+    s.orig = (int4 *)take(sizeof(int4) * own_cap);
+    s.mbar = (uint64_t *)take(16);
     s.rnd = (uint32_t *)take(sizeof(uint32_t) * 256);
     s.thr64 = (double *)take(sizeof(double) * 32);
     s.thr32 = (float *)take(sizeof(float) * 32);
@@ -1181,6 +1222,17 @@ __device__ __forceinline__ void load_tables(const DevState &d, ModelDev &md, Mix
     for (int i = threadIdx.x; i < (int)(sizeof(MixDev) / 4); i += blockDim.x) dst2[i] = src2[i];
 }
 
+// Once per launch, by the first thread of each group: the bulk-copy barrier
+// and its phase parity (the caller synchronises the block afterwards).
+__device__ __forceinline__ void init_group(unsigned char *gsmem, const DevState &d, int W)
+{
+    if (threadIdx.x % (32 * W) == 0) {
+        const Group G = carve(gsmem, d.stencil_cap, d.own_cap, W);
+        mbar_init(G.mbar);
+        G.misc[MS_PHASE] = 0;
+    }
+}
+
 // All n attempts of active cell g of the colour, by the 32 W threads of one
 // group (group index gid within the block, its shared memory at gsmem).
 template <int PREC, int W>
@@ -1192,8 +1244,8 @@ __device__ void run_cell(const DevState &d, int buf, int colour, const LogArgs &
     const int lane = threadIdx.x & 31;
     const int wig = gt >> 5;
     const int cap = d.stencil_cap;
-    const int rec_cap = d.full_rec ? cap : d.own_cap;
-    const Group G = carve(gsmem, cap, rec_cap, W);
+    const int own_cap = d.own_cap;
+    const Group G = carve(gsmem, cap, own_cap, W);
     const WarpScr S = warp_scr(G, wig);
 
     // ---- which cell ----
@@ -1244,13 +1296,23 @@ __device__ void run_cell(const DevState &d, int buf, int colour, const LogArgs &
         if (lane == 0) {
             G.misc[MS_N] = cnt;
             G.misc[MS_START] = cst;
+            G.misc[MS_FAIL] = 0;
+        }
+        // the raw records of the neighbourhood: one bulk copy per cell, all
+        // completing on the group's barrier (only when they fit)
+        const int Kw = __shfl_sync(FULL, incl, 31), nw0 = __shfl_sync(FULL, cnt, 0);
+        if (Kw + PADS <= cap && nw0 <= own_cap) {
+            if (lane == 0) mbar_arrive_expect(G.mbar, 16u * (unsigned)Kw);
+            __syncwarp();
+            if (lane < ns && cnt > 0) bulk_to_smem(G.rec + (incl - cnt), d.rec[buf] + cst, 16u * (unsigned)cnt, G.mbar);
         }
     }
     gsync<W>(gid);
     const int K = G.misc[MS_K];
     const int n = G.misc[MS_N];
     const int own_start = G.misc[MS_START];
-    if (K + PADS > cap || n > rec_cap) {
+    const unsigned parity = (unsigned)G.misc[MS_PHASE];
+    if (K + PADS > cap || n > own_cap) {   // no copy was issued
         if (gt == 0) {
             atomicOr(d.err, ERR_STENCIL);
             d.cell_dE[cellG] = 0.0;
@@ -1288,17 +1350,16 @@ __device__ void run_cell(const DevState &d, int buf, int colour, const LogArgs &
     c.r2q = raw ? c.pre_r2 : c.pre_r2 / c.h2f;
     const float rconf = rc2max * 1.0201f / c.h2f;   // (1.01 rc)^2, fixed-point units
     c.rv.smem = G.rec;
-    c.rv.full = d.full_rec != 0;
+    c.rv.full = true;
     c.rv.n = n;
     c.rv.gsrc = d.rec[buf];
     c.rv.cstart = G.cstart;
     c.rv.coff = G.coff;
     c.rv.ns = ns;
 
-    // ---- stage: issue every load of a thread (records, and the random words of
-    // the first 32 attempts) before using any ----
+    // ---- stage: the random words of the first 32 attempts load while the
+    // bulk copies land; then the records are split into the screening arrays ----
     {
-        const int4 *src = d.rec[buf];
         const int a = gt;
         const bool has_rnd = gt < 32 && gt < n;
         uint4 rb0 = make_uint4(0, 0, 0, 0), rb1 = rb0;
@@ -1311,31 +1372,27 @@ __device__ void run_cell(const DevState &d, int buf, int colour, const LogArgs &
             if (PREC == MC_PREC_FP64) th64 = d.att_thr64[slot];
             else th32 = d.att_thr32[slot];
         }
-        constexpr int UNR = 4;
-        for (int base = gt; base < K; base += UNR * T) {
-            int4 rc[UNR];
-#pragma unroll
-            for (int u = 0; u < UNR; ++u) {
-                const int idx = base + u * T;
-                if (idx < K) {
-                    const int s = find_segment(G.coff, ns, idx);
-                    rc[u] = src[G.cstart[s] + (idx - G.coff[s])];
-                }
+        // bounded wait for the copies (every thread: the barrier's completion
+        // makes the copied bytes visible to the waiting thread); a thread that
+        // gives up marks the cell, and the group leaves it together below
+        unsigned spins = 0;
+        bool ok = true;
+        while (!mbar_done(G.mbar, parity)) {
+            if (++spins > (1u << 22)) {
+                ok = false;
+                break;
             }
-#pragma unroll
-            for (int u = 0; u < UNR; ++u) {
-                const int idx = base + u * T;
-                if (idx < K) {
-                    if (idx < rec_cap) G.rec[idx] = rc[u];
-                    if (idx < n) G.orig[idx] = rc[u];
-                    G.sw[idx] = rc[u].w;
-                    const HiLo hl = hilo_of(c, Q3{(uint32_t)rc[u].x, (uint32_t)rc[u].y, (uint32_t)rc[u].z});
-                    G.sx[idx] = hl.x;
-                    G.sy[idx] = hl.y;
-                    G.sz[idx] = hl.z;
-                    G.sl[idx] = hl.lo;
-                }
-            }
+        }
+        if (!ok) G.misc[MS_FAIL] = 1;
+        for (int idx = gt; ok && idx < K; idx += T) {
+            const int4 rc = G.rec[idx];
+            if (idx < n) G.orig[idx] = rc;
+            G.sw[idx] = rc.w;
+            const HiLo hl = hilo_of(c, Q3{(uint32_t)rc.x, (uint32_t)rc.y, (uint32_t)rc.z});
+            G.sx[idx] = hl.x;
+            G.sy[idx] = hl.y;
+            G.sz[idx] = hl.z;
+            G.sl[idx] = hl.lo;
         }
         if (has_rnd) {
             uint4 *wv = (uint4 *)(G.rnd + 8 * a);
@@ -1353,10 +1410,19 @@ __device__ void run_cell(const DevState &d, int buf, int colour, const LogArgs &
             G.sz[i] = FAR;
             G.sl[i] = 0;
             G.sw[i] = PAD_W;
-            if (i < rec_cap) G.rec[i] = make_int4(0, 0, 0, PAD_W);
+            G.rec[i] = make_int4(0, 0, 0, PAD_W);
         }
     }
     gsync<W>(gid);
+    if (G.misc[MS_FAIL]) {
+        // copies that never completed: record it, give them one more bounded
+        // wait, and leave the cell untouched
+        if (gt == 0) atomicOr(d.err, ERR_TIMEOUT);
+        for (unsigned t2 = 0; t2 < (1u << 22) && !mbar_done(G.mbar, parity); ++t2) {
+        }
+        return;
+    }
+    if (gt == 0) G.misc[MS_PHASE] = (int)(parity ^ 1u);   // every thread has read the parity
 
     Tally t{};
     for (int a0 = 0; a0 < n; a0 += 32) {
@@ -1466,13 +1532,14 @@ __global__ void __launch_bounds__(BLOCK, W == 1 ? 3 : 1) phase_kernel(DevState d
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ ModelDev md;
     __shared__ MixDev mx;
+    const int gid = threadIdx.x / (32 * W);
+    unsigned char *gsmem = smem + (size_t)gid * group_bytes(d.stencil_cap, d.own_cap, W);
+    init_group(gsmem, d, W);
     load_tables(d, md, mx);
     __syncthreads();
-    const int gid = threadIdx.x / (32 * W);
     const int g = blockIdx.x * CPB + gid;
     if (g >= d.n_act) return;          // whole group leaves together
-    const int rec_cap = d.full_rec ? d.stencil_cap : d.own_cap;
-    run_cell<PREC, W>(d, buf, colour, lg, g, md, mx, smem + (size_t)gid * group_bytes(d.stencil_cap, rec_cap, W), gid);
+    run_cell<PREC, W>(d, buf, colour, lg, g, md, mx, gsmem, gid);
 }
 
 // Per replica (one block of BLOCK threads): add the sweep's accepted Delta E,
@@ -1576,14 +1643,14 @@ __global__ void __launch_bounds__(BLOCK, W == 1 ? 3 : 1) sweep_persistent(DevSta
     __shared__ MixDev mx;
     __shared__ double red[BLOCK];
     __shared__ int tmp[BLOCK / 32];
+    const int gid = threadIdx.x / T;
+    unsigned char *gsmem = smem + (size_t)gid * group_bytes(d.stencil_cap, d.own_cap, W);
+    init_group(gsmem, d, W);
     load_tables(d, md, mx);
     __syncthreads();
     const int nthr = gridDim.x * BLOCK;
     const int tid = blockIdx.x * BLOCK + threadIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int gid = threadIdx.x / T;
-    const int rec_cap = d.full_rec ? d.stencil_cap : d.own_cap;
-    unsigned char *gsmem = smem + (size_t)gid * group_bytes(d.stencil_cap, rec_cap, W);
     const LogArgs none{nullptr, 0, 0};
     const int nC = d.n_cells;
     const int chunk = (nC + gridDim.x - 1) / gridDim.x;
@@ -1645,9 +1712,9 @@ __global__ void __launch_bounds__(BLOCK, W == 1 ? 3 : 1) sweep_persistent(DevSta
     }
 }
 
-size_t phase_smem_bytes(int stencil_cap, int rec_cap, int warps_per_cell)
+size_t phase_smem_bytes(int stencil_cap, int own_cap, int warps_per_cell)
 {
-    return group_bytes(stencil_cap, rec_cap, warps_per_cell) * (size_t)(BLOCK / (32 * warps_per_cell));
+    return group_bytes(stencil_cap, own_cap, warps_per_cell) * (size_t)(BLOCK / (32 * warps_per_cell));
 }
 
 template <class K>
@@ -1692,8 +1759,7 @@ static void launch_prec(const DevState &d, int buf, int W, const LogArgs &lg, cu
 {
     const int cpb = BLOCK / (32 * W);
     const int blocks = (d.n_act + cpb - 1) / cpb;
-    const int rec_cap = d.full_rec ? d.stencil_cap : d.own_cap;
-    const size_t sm = phase_smem_bytes(d.stencil_cap, rec_cap, W);
+    const size_t sm = phase_smem_bytes(d.stencil_cap, d.own_cap, W);
     for (int colour = 0; colour < 8; ++colour) {
         if (W == 4) phase_kernel<PREC, 4><<<blocks, BLOCK, sm, st>>>(d, buf, colour, lg);
         else if (W == 2) phase_kernel<PREC, 2><<<blocks, BLOCK, sm, st>>>(d, buf, colour, lg);
@@ -1737,8 +1803,7 @@ int persistent_grid(const DevState &d, int warps_per_cell, int max_blocks)
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
     if (!coop) return 0;
-    const int rec_cap = d.full_rec ? d.stencil_cap : d.own_cap;
-    const size_t sm = phase_smem_bytes(d.stencil_cap, rec_cap, warps_per_cell);
+    const size_t sm = phase_smem_bytes(d.stencil_cap, d.own_cap, warps_per_cell);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_kernel(d.precision, warps_per_cell), BLOCK,
                                                       sm) != cudaSuccess)
         return 0;
@@ -1752,8 +1817,7 @@ int persistent_grid(const DevState &d, int warps_per_cell, int max_blocks)
 int launch_persistent(const DevState &d, int buf, int n_sweeps, int warps_per_cell, int grid, unsigned int *bar,
                       int *scan_tot, cudaStream_t st)
 {
-    const int rec_cap = d.full_rec ? d.stencil_cap : d.own_cap;
-    const size_t sm = phase_smem_bytes(d.stencil_cap, rec_cap, warps_per_cell);
+    const size_t sm = phase_smem_bytes(d.stencil_cap, d.own_cap, warps_per_cell);
     GridBar gb{bar, scan_tot};
     DevState dd = d;
     void *args[] = {(void *)&dd, (void *)&buf, (void *)&n_sweeps, (void *)&gb};
