@@ -56,6 +56,10 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--autotune", type=int, default=4,
+                    help="sweeps per schedule for mc_autotune when the schedule is automatic (0: off)")
+    ap.add_argument("--one-by-one", type=int, default=16,
+                    help="batched workloads: replicas timed one by one on their own handles (0: off)")
     return ap.parse_args()
 
 
@@ -187,6 +191,34 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_one_by_one(F, wl, mix, sps, n_take, precision):
+    """Moves/s of a sample of the batched replicas, each on its own handle and
+    run one after the other (same sweeps per step, CUDA events per handle)."""
+    import torch
+    n_mol = wl["n_mol"]
+    offs = np.concatenate([[0], np.cumsum(3 * n_mol)])
+    take = np.linspace(0, len(n_mol) - 1, min(n_take, len(n_mol))).astype(int)
+    total_ms, total_att = 0.0, 0
+    for k in take:
+        sl = slice(offs[k], offs[k + 1])
+        hk = F.Handle(float(wl["L"][k]), wl["xyz"][sl], wl["types"][sl], W.PAPER_POT, precision=precision)
+        st = torch.cuda.Stream()
+        hk.set_stream(st.cuda_stream)
+        hk.sweep(sps, float(wl["T"][k]), mix, int(wl["seeds"][k]))      # warm-up (first launch)
+        a0 = sum(hk.stats()[0]["attempts"])
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        hk.sweep(sps, float(wl["T"][k]), mix, int(wl["seeds"][k]))
+        e1.record(st)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+        total_att += sum(hk.stats()[0]["attempts"]) - a0
+        hk.close()
+    return {"value": total_att / (total_ms / 1000.0), "unit": UNIT, "replicas_timed": int(len(take)),
+            "sweeps_each": sps, "what": "the same replicas, own handle each, one after the other"}
+
+
 def run_native(args):
     import torch
     from paper_2506_21290_gb300 import build as B
@@ -213,6 +245,12 @@ def run_native(args):
     h = F.Handle(wl["L"], wl["xyz"], wl["types"], W.PAPER_POT, precision=precision, device=local, n_mol=wl["n_mol"],
                  launch_mode=args.launch_mode, warps_per_cell=args.warps_per_cell, recheck_gap=args.recheck_gap)
     N = h.N
+    tuned = None
+    if args.autotune > 0 and args.warps_per_cell == 0 and args.launch_mode == 0:
+        # pick the cell schedule on a copy of the state (the chain is unchanged)
+        res = h.autotune(args.autotune, wl["T"], mix, wl["seeds"])
+        tuned = {"ms_per_sweep": {"persistent": [float(x) for x in res[:3]], "graphs": [float(x) for x in res[3:]]},
+                 "warps_per_cell": [1, 2, 4], "sweeps_per_trial": args.autotune}
     # a dedicated stream: the library enqueues on it, the events are recorded on it
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
@@ -283,6 +321,19 @@ def run_native(args):
     peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
     peak_at_clock = (SM_COUNT * FP32_LANES_PER_SM * 2 * clk["sm_mhz"] * 1e6 / 1e12) if clk.get("sm_mhz") else None
 
+    # drift of the FP64 running total against a full FP64 recompute
+    E_rec = h.energy()
+    st_now = h.stats()
+    drift = max(abs(st_now[r]["e_run"] - E_rec[r]) / max(abs(E_rec[r]), 1e-300) for r in range(h.n_rep))
+    energy_drift = {"sweeps": int(st_now[0]["sweeps"]), "max_rel": drift,
+                    "what": "|running FP64 total - FP64 recompute| / |recompute|, worst replica"}
+
+    # the same replicas, each on its own handle and run one after the other
+    one_by_one = None
+    if wl["replicas"] > 1 and args.one_by_one > 0 and rank == 0:
+        one_by_one = run_one_by_one(F, wl, mix, sps, args.one_by_one, precision)
+        one_by_one["batched_over_one_by_one"] = value / one_by_one["value"]
+
     # end to end through the C ABI with host buffers
     e2e = None
     if args.e2e_steps > 0:
@@ -340,6 +391,11 @@ def run_native(args):
                                                             "finalize": stage_ms[2] / n_prof}},
         "cpu_baseline": cpu,
         "e2e": e2e,
+        "energy_drift": energy_drift,
+        "schedule": {"warps_per_cell": info["warps_per_cell"],
+                     "launch": "persistent" if persistent else "graph per sweep",
+                     "autotune": tuned},
+        "one_by_one": one_by_one,
         "gpu_launches": args.steps * ((1 + 1) if persistent else sps * launches_per_sweep) + args.steps * 2,
         "clocks": clk,
     }

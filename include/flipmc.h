@@ -293,6 +293,19 @@ int mc_observables(mc_handle *h, const double *qvec_atom, int n_qa, const double
                    double *out, double *fs_atom, double *fscm_mol, double *c2_mol);
 
 /* Static facts of the handle. */
+/* Pick the cell schedule: run n_sweeps sweeps (>= 1) with each schedule (1,
+ * 2 and 4 warps per cell, as one persistent launch per call and as one CUDA
+ * graph per sweep) from the same state, time them on the handle's stream and
+ * keep the fastest.  The state, the sweep counters, the running energies and
+ * the statistics are restored afterwards: the chain continues exactly as if
+ * the call had not been made (the schedule never changes the chain).  The
+ * arguments T, mix and seeds are those of mc_sweep_batch.  results (nullable,
+ * host, 6 doubles): ms per sweep for W = 1, 2, 4 persistent, then W = 1, 2, 4
+ * graphs; a schedule that cannot run reads -1.  Not part of the paper's method:
+ * an engineering choice of the library.  Errors: INVALID_ARG, CUDA. */
+int mc_autotune(mc_handle *h, int n_sweeps, const double *T, const mc_move_mix *mix, const uint64_t *seeds,
+                double *results);
+
 int mc_get_info(mc_handle *h, mc_info *info);
 
 /*

@@ -732,6 +732,94 @@ int mc_sweep_timed(mc_handle *h, int n_sweeps, const double *T, const mc_move_mi
     return check_device_errors(h);
 }
 
+// Switch the cell schedule: warps per cell W and the launch form.
+static int set_schedule(mc_handle *h, int W, bool persistent)
+{
+    const size_t sm = phase_smem_bytes(h->stencil_cap, h->own_cap, W);
+    if (sm > 220u * 1024u) return MC_ERR_INVALID_ARG;
+    if (phase_set_smem_limit((int)sm) != 0) return MC_ERR_CUDA;
+    if (W != h->wpb)
+        for (int b = 0; b < 2; ++b)
+            if (h->graph[b]) {
+                cudaGraphExecDestroy(h->graph[b]);
+                h->graph[b] = nullptr;
+            }
+    h->wpb = W;
+    h->smem_bytes = sm;
+    h->pgrid = persistent ? persistent_grid(h->ds, W, kMaxPersistentBlocks) : 0;
+    return (persistent && h->pgrid == 0) ? MC_ERR_INVALID_ARG : MC_OK;
+}
+
+int mc_autotune(mc_handle *h, int n_sweeps, const double *T, const mc_move_mix *mix, const uint64_t *seeds,
+                double *results)
+{
+    if (!h || !T || !seeds || n_sweeps < 1) return fail(MC_ERR_INVALID_ARG, "bad arguments");
+    int rc = check_mix(mix);
+    if (rc) return rc;
+    if ((rc = set_device(h))) return rc;
+    // device snapshot of everything a sweep changes
+    const size_t n = (size_t)h->n_sites, R = (size_t)h->n_rep;
+    const size_t b_rec = sizeof(int4) * n, b_img = sizeof(int) * 3 * n, b_e = sizeof(double) * R,
+                 b_st = sizeof(unsigned long long) * STAT_N * R, b_ct = sizeof(RepCtr) * R;
+    unsigned char *snap = nullptr;
+    CUDA_TRY(cudaMalloc(&snap, b_rec + b_img + b_e + b_st + b_ct));
+    const int cur0 = h->cur, W0 = h->wpb;
+    const bool p0 = h->pgrid > 0;
+    auto copy_all = [&](bool save) {
+        void *dev[5] = {h->ds.rec[cur0], h->ds.img, h->ds.e_run, h->ds.stats, h->ds.ctr};
+        const size_t sz[5] = {b_rec, b_img, b_e, b_st, b_ct};
+        size_t off = 0;
+        for (int k = 0; k < 5; ++k) {
+            if (save) cudaMemcpyAsync(snap + off, dev[k], sz[k], cudaMemcpyDeviceToDevice, h->stream);
+            else cudaMemcpyAsync(dev[k], snap + off, sz[k], cudaMemcpyDeviceToDevice, h->stream);
+            off += sz[k];
+        }
+        h->cur = cur0;
+    };
+    copy_all(true);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int Ws[3] = {1, 2, 4};
+    double best = 1e300;
+    int bestW = W0;
+    bool bestP = p0;
+    for (int form = 0; form < 2; ++form) {
+        for (int k = 0; k < 3; ++k) {
+            double ms = -1.0;
+            if (set_schedule(h, Ws[k], form == 0) == MC_OK) {
+                copy_all(false);
+                rc = sweep_impl(h, 1, T, mix, seeds, false);   // first use: graph capture, caches
+                if (rc == MC_OK) {
+                    copy_all(false);
+                    cudaEventRecord(e0, h->stream);
+                    rc = sweep_impl(h, n_sweeps, T, mix, seeds, false);
+                    cudaEventRecord(e1, h->stream);
+                }
+                if (rc == MC_OK && cudaEventSynchronize(e1) == cudaSuccess) {
+                    float f = 0.f;
+                    cudaEventElapsedTime(&f, e0, e1);
+                    ms = f / n_sweeps;
+                    if (ms < best) {
+                        best = ms;
+                        bestW = Ws[k];
+                        bestP = form == 0;
+                    }
+                }
+            }
+            if (results) results[3 * form + k] = ms;
+        }
+    }
+    copy_all(false);
+    rc = set_schedule(h, bestW, bestP);
+    cudaStreamSynchronize(h->stream);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(snap);
+    if (rc) return fail(rc, "autotune: cannot restore the chosen schedule");
+    return check_device_errors(h);
+}
+
 int mc_energy_device(mc_handle *h, double *dev_E_out)
 {
     if (!h || !dev_E_out) return fail(MC_ERR_INVALID_ARG, "NULL argument");

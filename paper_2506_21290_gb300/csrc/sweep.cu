@@ -177,10 +177,14 @@ __device__ __forceinline__ bool mbar_done(uint64_t *mb, unsigned parity)
     return ok != 0;
 }
 
-// bytes (a multiple of 16, both addresses 16-byte aligned) from global to shared
+// bytes (a multiple of 16, both addresses 16-byte aligned) from global to
+// shared.  The proxy fence orders this group's earlier generic accesses to the
+// destination before the copy's writes; the source was written before the
+// last grid-wide barrier (or kernel boundary), whose gpu-scope fences put it
+// in L2, where the copy reads it.
 __device__ __forceinline__ void bulk_to_smem(void *dst, const void *src, unsigned bytes, uint64_t *mb)
 {
-    asm volatile("fence.proxy.async;\n\t"
+    asm volatile("fence.proxy.async.shared::cta;\n\t"
                  "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                      smem_u32(dst)),
                  "l"(src), "r"(bytes), "r"(smem_u32(mb))

@@ -95,6 +95,7 @@ def load():
         "mc_sync": ([vp], i32),
         "mc_energy_device": ([vp, vp], i32),
         "mc_sweep_timed": ([vp, i32, vp, vp, vp, vp], i32),
+        "mc_autotune": ([vp, i32, vp, vp, vp, vp], i32),
         "mc_energy": ([vp, vp], i32),
         "mc_state": ([vp, vp, vp, vp], i32),
         "mc_state_fixed": ([vp, vp, vp, vp], i32),
@@ -215,6 +216,15 @@ def mc_sweep_timed(h, n, Ts, mix, seeds):
     m = make_mix(mix)
     _check(load().mc_sweep_timed(h, int(n), _ptr(Ts), C.byref(m), _ptr(seeds), _ptr(ms)), "mc_sweep_timed")
     return ms
+
+
+def mc_autotune(h, n, Ts, mix, seeds):
+    Ts = np.ascontiguousarray(np.atleast_1d(Ts), dtype=np.float64)
+    seeds = np.ascontiguousarray(np.atleast_1d(seeds), dtype=np.uint64)
+    res = np.zeros(6, dtype=np.float64)
+    m = make_mix(mix)
+    _check(load().mc_autotune(h, int(n), _ptr(Ts), C.byref(m), _ptr(seeds), _ptr(res)), "mc_autotune")
+    return res
 
 
 def mc_sync(h):
@@ -352,6 +362,15 @@ class Handle:
         Ts = np.broadcast_to(np.asarray(T, dtype=np.float64), (self.n_rep,))
         seeds = np.broadcast_to(np.asarray(seed, dtype=np.uint64), (self.n_rep,))
         return mc_sweep_timed(self.h, n, Ts, mix, seeds)
+
+    def autotune(self, n, T, mix, seed):
+        """Time every cell schedule on a copy of the state and keep the fastest;
+        returns ms per sweep [W=1, 2, 4 persistent, W=1, 2, 4 graphs] (-1: unavailable)."""
+        Ts = np.broadcast_to(np.asarray(T, dtype=np.float64), (self.n_rep,))
+        seeds = np.broadcast_to(np.asarray(seed, dtype=np.uint64), (self.n_rep,))
+        res = mc_autotune(self.h, n, Ts, mix, seeds)
+        self.info = mc_get_info(self.h)
+        return res
 
     def energy_device(self, dev_ptr):
         mc_energy_device(self.h, dev_ptr)

@@ -200,6 +200,37 @@ def test_runs_are_reproducible_and_resumable():
     assert np.array_equal(d.state_fixed()[0], q4)
 
 
+@pytest.mark.parametrize("precision,M", [("fp32", 343), ("fp64", 125)])
+def test_autotune_leaves_the_chain_unchanged(precision, M):
+    """mc_autotune times every schedule from a snapshot and restores it: the
+    chain after it is the chain without it, bit for bit (positions, types,
+    decisions); only the cell schedule may differ."""
+    L, xyz, t = _start(M, 41)
+    a = F.Handle(L, xyz, t, POT, precision=precision)
+    b = F.Handle(L, xyz, t, POT, precision=precision)
+    for h in (a, b):
+        h.sweep(3, 1.4, W.PAPER_MIX, 23)
+    res = a.autotune(3, 1.4, W.PAPER_MIX, 23)
+    assert res.shape == (6,) and (res > 0).any()
+    assert a.info["warps_per_cell"] in (1, 2, 4)
+    ms = {(1, True): res[0], (2, True): res[1], (4, True): res[2], (1, False): res[3], (2, False): res[4],
+          (4, False): res[5]}
+    chosen = ms[(a.info["warps_per_cell"], a.info["persistent_blocks"] > 0)]
+    assert chosen == min(v for v in res if v > 0)
+    for h in (a, b):
+        h.sweep(5, 1.4, W.PAPER_MIX, 23)
+        h.sweep(2, 2.2, W.RIGID_MIX, 24)
+    qa, Xa, ta = a.state_fixed()
+    qb, Xb, tb = b.state_fixed()
+    assert np.array_equal(qa, qb) and np.array_equal(Xa, Xb) and np.array_equal(ta, tb)
+    sa, sb = a.stats()[0], b.stats()[0]
+    for k in ("attempts", "accepts", "rejected_geometry", "rejected_bond", "fp64_rechecks", "sweeps"):
+        assert sa[k] == sb[k], k
+    # the running energy sums the same accepted Delta E; in FP32 mode a cell's
+    # FP32 partial sums depend on how its attempts were spread over warps
+    assert sa["e_run"] == pytest.approx(sb["e_run"], rel=1e-9, abs=1e-6)
+
+
 @pytest.mark.parametrize("precision,wpc,M", [("fp64", 1, 125), ("fp32", 1, 343), ("fp32", 2, 343), ("fp32", 4, 1000),
                                              ("fp64", 4, 216)])
 def test_persistent_launch_matches_graphs(precision, wpc, M):
