@@ -38,6 +38,10 @@ SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
 L2_FLUSH_BYTES = 256 << 20
+# DRAM bytes (read + write) per launch of the dominant kernel from the ncu capture summarised in
+# profiles/sweep_persistent_single-1000_full.md; keyed by (workload, kernel, sweeps per launch), so a timed
+# launch that differs from the captured one reports null
+NCU_TRAFFIC = {("single-1000", "sweep_persistent<FP32,W=4>", 100): 280064}
 
 
 def parse():
@@ -321,6 +325,10 @@ def run_native(args):
     peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
     peak_at_clock = (SM_COUNT * FP32_LANES_PER_SM * 2 * clk["sm_mhz"] * 1e6 / 1e12) if clk.get("sm_mhz") else None
 
+    kernel_name = ("sweep_persistent" if persistent else "phase_kernel") + \
+        ("<FP32,W=%d>" if precision == "fp32" else "<FP64,W=%d>") % info["warps_per_cell"]
+    traffic = NCU_TRAFFIC.get((args.workload, kernel_name, sps)) if persistent else None
+
     # drift of the FP64 running total against a full FP64 recompute
     E_rec = h.energy()
     st_now = h.stats()
@@ -379,10 +387,9 @@ def run_native(args):
         "acceptance": [accepts[k] / att_k[k] if att_k[k] else None for k in range(4)],
         "geometry_reject_rate": geom / max(attempts, 1),
         "roofline": {"bound": "alu",
-                     "kernel": ("sweep_persistent" if persistent else "phase_kernel")
-                               + ("<FP32,W=%d>" if precision == "fp32" else "<FP64,W=%d>") % info["warps_per_cell"],
+                     "kernel": kernel_name,
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": None, "peak_basis": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (max clock)",
+                     "traffic": traffic, "traffic_unit": "B per launch (ncu dram__bytes_read + write)", "peak_basis": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (max clock)",
                      "peak_at_measured_clock": peak_at_clock,
                      "launch_ms": launch_ms, "flops_per_launch": flops_per_launch,
                      "flops_per_pair_eval": FLOPS_PER_PAIR_EVAL,

@@ -118,6 +118,33 @@ def test_fp32_same_decisions_and_dE_within_tolerance(M, seed, T, mix, wpc):
     assert np.array_equal(lg["dE64"][re & ev], lo["dE"][re & ev])     # rechecks are the exact FP64 value
 
 
+# FP32 Delta E error bound that the default recheck margin (1e-5 of the summed
+# magnitudes) relies on: distances to 7-9 units of FP32 rounding, each term's
+# sensitivity to them (at most 6x its magnitude for WCA), its own evaluation
+# (about 31 units) and the sums (at most 21 units) give <= 106 u = 6.3e-6.
+FP32_DE_BOUND = 6.3e-6
+
+
+@pytest.mark.parametrize("M,seed,T,mix", [(343, 51, 1.1, W.PAPER_MIX), (216, 52, 0.75, W.RIGID_MIX),
+                                          (64, 53, 2.0, W.RIGID_MIX)])
+def test_fp32_error_within_derived_bound(M, seed, T, mix):
+    """Every FP32 Delta E is within FP32_DE_BOUND x (its summed term
+    magnitudes) of the oracle's FP64 value, on the split-coordinate path and
+    on the n_c = 2 raw-record path; so with the default margin no decision
+    taken in FP32 can differ from the FP64 one."""
+    L, xyz, t = _start(M, seed)
+    h = F.Handle(L, xyz, t, POT, precision="fp32")
+    ch = oracle.Chain(L, xyz, t, POT, nc=h.info["max_cells_per_axis"])
+    assert h.info["recheck_gap"] == pytest.approx(1e-5)
+    lg = h.sweep_logged(20, T, mix, seed)
+    lo = ch.run(20, T, mix, seed=seed, log=True)
+    assert np.array_equal(lg["accepted"], lo["accepted"])
+    ev = (lo["status"] == 0) & ((lg["flags"] & 1) == 0)
+    assert ev.sum() > 1000
+    err = np.abs(lg["dE"][ev] - lo["dE"][ev])
+    assert np.all(err <= FP32_DE_BOUND * lg["scale"][ev]), (err / lg["scale"][ev]).max()
+
+
 def test_energy_matches_brute_force():
     for M in (64, 343, 1000):
         L, xyz, t = _start(M, 9)
