@@ -35,20 +35,44 @@ __device__ __forceinline__ void cl_scatter_item(const DevState &d, int buf_in, i
     d.rec[buf_out][d.cell_start[d.cell_of[g]] + d.slot_of[g]] = d.rec[buf_in][g];
 }
 
-// The random words and Metropolis threshold of every attempt of the sweep.
-// Attempt a of cell c (a < occupancy) is slot start(c) + a; its words are the
-// Philox blocks (2a, c, sweep) and (2a+1, c, sweep) under the replica's seed;
-// its threshold is -T ln u with u = (2 u52 + 1) 2^-53 from the first block.
-__device__ __forceinline__ void attempt_randoms(const DevState &d, int r, int cellL, int slot, int a)
+// The random draws and the Metropolis threshold of every attempt of the sweep.
+// Attempt a of cell c (a < occupancy n) is slot start(c) + a; its words are
+// the Philox blocks (2a, c, sweep) and (2a+1, c, sweep) under the replica's
+// seed, w0..w7.  Everything that does not depend on the state is decoded here,
+// off the serial attempt chain:
+//   quad 0: x = site rank (w0 n) >> 32 | move type (integer thresholds on w1)
+//           << 16 | flip axis (w7 3) >> 32 << 18;
+//           y, z, w = the displacement drawn from w4, w5, w6 (atom step for a
+//           translation, molecule step for a molecule translation), or w4, w5,
+//           w6 themselves for a rotation;
+//   quad 1: x, y = w2, w3 (u = (2 u52 + 1) 2^-53 of the threshold), z, w = 0;
+// and the threshold -T ln u (FP64 series in FP64 mode, __logf in FP32 mode).
+__device__ __forceinline__ void attempt_randoms(const DevState &d, int r, int cellL, int slot, int a, int n)
 {
     const uint64_t sweep = d.ctr[r].sweep;
-    const uint64_t seed = d.par[r].seed;
-    const U4 b0 = rng_block((uint32_t)(2 * a), (uint32_t)cellL, sweep, seed);
-    const U4 b1 = rng_block((uint32_t)(2 * a + 1), (uint32_t)cellL, sweep, seed);
-    d.att_rnd[2 * (size_t)slot] = make_uint4(b0.x, b0.y, b0.z, b0.w);
-    d.att_rnd[2 * (size_t)slot + 1] = make_uint4(b1.x, b1.y, b1.z, b1.w);
+    const RepParam par = d.par[r];
+    const U4 b0 = rng_block((uint32_t)(2 * a), (uint32_t)cellL, sweep, par.seed);
+    const U4 b1 = rng_block((uint32_t)(2 * a + 1), (uint32_t)cellL, sweep, par.seed);
+    const MixDev mx = *d.mix;
+    const int k = (int)(((unsigned long long)b0.x * (unsigned long long)n) >> 32);
+    const int mvt = move_type(b0.y, mx);
+    const int axis = (int)(((unsigned long long)b1.w * 3ull) >> 32);
+    uint4 q0;
+    q0.x = (uint32_t)k | ((uint32_t)mvt << 16) | ((uint32_t)axis << 18);
+    if (mvt == MC_MOVE_MOL_ROT) {
+        q0.y = b1.x;
+        q0.z = b1.y;
+        q0.w = b1.z;
+    } else {
+        const int32_t D = mvt == MC_MOVE_MOL_TRANS ? par.D_mol : par.D_atom;
+        q0.y = (uint32_t)uniform_disp(b1.x, D);
+        q0.z = (uint32_t)uniform_disp(b1.y, D);
+        q0.w = (uint32_t)uniform_disp(b1.z, D);
+    }
+    d.att_rnd[2 * (size_t)slot] = q0;
+    d.att_rnd[2 * (size_t)slot + 1] = make_uint4(b0.z, b0.w, 0u, 0u);
     const unsigned long long u52 = ((unsigned long long)b0.z << 20) | (unsigned long long)(b0.w >> 12);
-    const double T = d.par[r].T;
+    const double T = par.T;
     if (d.precision == MC_PREC_FP64) {
         const double u = __dmul_rn((double)(2ull * u52 + 1ull), 0x1p-53);
         d.att_thr64[slot] = -__dmul_rn(T, ln_series(u));
@@ -70,7 +94,7 @@ __device__ __forceinline__ void cl_order_cell(const DevState &d, int buf, int c,
     if (d.att_rnd != nullptr && n > 0) {
         const int r = d.rep_of_site[start];
         const int cellL = c - d.rep[r].cell_off;
-        for (int a = lane; a < n; a += 32) attempt_randoms(d, r, cellL, start + a, a);
+        for (int a = lane; a < n; a += 32) attempt_randoms(d, r, cellL, start + a, a, n);
     }
     if (n <= 1) return;
     if (n <= 32) {

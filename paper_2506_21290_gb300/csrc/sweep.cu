@@ -872,7 +872,6 @@ struct CellCtx {
     float pre_r2;           // screening radius squared (sigma units): 1.01 x the largest WCA cutoff squared
     float r2q;              // the same in the units of the screens (fixed-point units squared unless raw)
     float gap, T32;
-    int32_t D_atom, D_mol;
     int *err;
 };
 
@@ -888,13 +887,16 @@ template <int PREC, int W>
 __device__ Res evaluate(const CellCtx &cx, const Group &G, const WarpScr &S, Near *N, int jr, int lane)
 {
     const ModelDev &md = *cx.md;
+    // the attempt's draws, decoded by the cell-list build (site rank, move type,
+    // flip axis, integer displacement or rotation words; threshold words)
     const uint32_t *w = G.rnd + 8 * jr;
-    const int n = cx.n, K = cx.K;
-    const int k = (int)(((unsigned long long)w[0] * (unsigned long long)n) >> 32);
+    const uint4 dsc = *(const uint4 *)w;
+    const int K = cx.K, n = cx.n;
+    const int k = (int)(dsc.x & 0xFFFFu);
+    const int mvt = (int)((dsc.x >> 16) & 3u);
     const int4 rk = G.rec[k];
     const int wi = rk.w;
     const int mol = rec_mol(wi);
-    const int mvt = move_type(w[1], *cx.mx);
     int status = MC_ST_EVALUATED;
     int flags = 0, accept = 0;
     float scale = 0.f, dE32 = 0.f;
@@ -906,8 +908,7 @@ __device__ Res evaluate(const CellCtx &cx, const Group &G, const WarpScr &S, Nea
     int nmv = 1;
     if (mvt == MC_MOVE_ATOM) {
         qo[0] = Q3{(uint32_t)rk.x, (uint32_t)rk.y, (uint32_t)rk.z};
-        qn[0] = Q3{qo[0].x + (uint32_t)uniform_disp(w[4], cx.D_atom), qo[0].y + (uint32_t)uniform_disp(w[5], cx.D_atom),
-                   qo[0].z + (uint32_t)uniform_disp(w[6], cx.D_atom)};
+        qn[0] = Q3{qo[0].x + dsc.y, qo[0].y + dsc.z, qo[0].z + dsc.w};
         t3o[0] = t3n[0] = rec_type(wi);
         if (cell_local(qn[0].x, qn[0].y, qn[0].z, cx.shift, cx.nc) != cx.cellL) status = MC_ST_LEFT_CELL;
     } else {
@@ -923,7 +924,7 @@ __device__ Res evaluate(const CellCtx &cx, const Group &G, const WarpScr &S, Nea
             }
         }
         if (mvt == MC_MOVE_FLIP) {
-            const int axis = (int)(((unsigned long long)w[7] * 3ull) >> 32);
+            const int axis = (int)((dsc.x >> 18) & 3u);
             const int kp = axis == 0 ? k1 : k0, kq = axis == 2 ? k1 : k2;
             if (kp < 0 || kq < 0) {
                 status = MC_ST_NOT_IN_CELL;
@@ -954,11 +955,8 @@ __device__ Res evaluate(const CellCtx &cx, const Group &G, const WarpScr &S, Nea
                     t3o[s] = t3n[s] = rec_type(rs.w);
                 }
                 if (mvt == MC_MOVE_MOL_TRANS) {
-                    const int32_t dx = uniform_disp(w[4], cx.D_mol), dy = uniform_disp(w[5], cx.D_mol),
-                                  dz = uniform_disp(w[6], cx.D_mol);
 #pragma unroll
-                    for (int s = 0; s < 3; ++s)
-                        qn[s] = Q3{qo[s].x + (uint32_t)dx, qo[s].y + (uint32_t)dy, qo[s].z + (uint32_t)dz};
+                    for (int s = 0; s < 3; ++s) qn[s] = Q3{qo[s].x + dsc.y, qo[s].y + dsc.z, qo[s].z + dsc.w};
                 } else {
                     uint32_t a9[9];
                     if (lane == 0) {
@@ -968,7 +966,7 @@ __device__ Res evaluate(const CellCtx &cx, const Group &G, const WarpScr &S, Nea
                             qq[s][1] = qo[s].y;
                             qq[s][2] = qo[s].z;
                         }
-                        rotate_molecule(qq, qr, w + 4, cx.mx->rot_a, cx.h, cx.inv_h);
+                        rotate_molecule(qq, qr, w + 1, cx.mx->rot_a, cx.h, cx.inv_h);
                         for (int s = 0; s < 3; ++s)
                             for (int ax = 0; ax < 3; ++ax) a9[3 * s + ax] = qr[s][ax];
                     }
@@ -1071,7 +1069,7 @@ __device__ Res evaluate(const CellCtx &cx, const Group &G, const WarpScr &S, Nea
                 // retake in FP64: exact Delta E against the exact threshold
                 flags = 1;
                 __syncwarp();
-                const unsigned long long u52 = ((unsigned long long)w[2] << 20) | (unsigned long long)(w[3] >> 12);
+                const unsigned long long u52 = ((unsigned long long)w[4] << 20) | (unsigned long long)(w[5] >> 12);
                 const double u = __dmul_rn((double)(2ull * u52 + 1ull), 0x1p-53);
                 const double thr = -__dmul_rn(cx.T64, ln_series(u));
                 const int dec = exact(thr, nq64);
@@ -1344,8 +1342,6 @@ __device__ void run_cell(const DevState &d, int buf, int colour, const LogArgs &
     c.h2f = ri.h2f;
     c.T64 = dy.T;
     c.T32 = dy.T32;
-    c.D_atom = dy.D_atom;
-    c.D_mol = dy.D_mol;
     c.gap = md.recheck_gap_f;
     c.err = d.err;
     float rc2max = 0.f;
