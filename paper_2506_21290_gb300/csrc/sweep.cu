@@ -1584,7 +1584,11 @@ struct GridBar {
 
 // Arrive, then wait until every block has arrived as often as this one.  The
 // count only grows, so no reset is needed between barriers; `target` is the
-// caller's running total (thread 0 only).  The wait is bounded.
+// caller's running total (thread 0 only).  The arrival is a release at gpu
+// scope (it publishes every write the block made before the __syncthreads
+// above it) and the polls are acquires (the block's reads after the
+// __syncthreads below see every other block's published writes).  The wait is
+// bounded.
 __device__ bool grid_sync(const GridBar &gb, unsigned int &target, int *err)
 {
     __shared__ int ok;
@@ -1592,8 +1596,7 @@ __device__ bool grid_sync(const GridBar &gb, unsigned int &target, int *err)
     if (threadIdx.x == 0) {
         ok = 1;
         target += gridDim.x;
-        __threadfence();
-        atomicAdd(gb.count, 1u);
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(gb.count) : "memory");
         unsigned long long spins = 0;
         for (;;) {
             unsigned int v;
@@ -1605,7 +1608,6 @@ __device__ bool grid_sync(const GridBar &gb, unsigned int &target, int *err)
                 break;
             }
         }
-        __threadfence();
     }
     __syncthreads();
     return ok != 0;
