@@ -1048,6 +1048,15 @@ int mc_get_info(mc_handle *h, mc_info *info)
     return MC_OK;
 }
 
+}  // extern "C"
+
+int flipmc::record_error(int code, const char *msg)
+{
+    return fail(code, msg);
+}
+
+extern "C" {
+
 const char *mc_last_error(void)
 {
     return g_err.c_str();

@@ -3,8 +3,8 @@
 // memory.
 //
 // Some callers cannot call cudaMalloc: code that runs inside another
-// framework's memory pool or under a strict device-memory budget, code that is
-// being captured into a CUDA graph by someone else, or embedded callers that
+// framework's memory pool (which owns the device memory and must not be
+// bypassed), code under a fixed device-memory budget, or embedded callers that
 // are only allowed to enqueue kernels on a stream they were handed.  For them
 // the working space of the cell-list build and of the energy reduction lives
 // in one file-scope __device__ array, sized for up to kMaxSites atoms and
@@ -60,12 +60,10 @@ constexpr size_t kScratchBytes = al256(kOffESite + sizeof(double) * kMaxSites);
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
-thread_local std::string g_noalloc_err;
-
+// errors go where mc_last_error() reads them
 int noalloc_fail(int code, const char *msg)
 {
-    g_noalloc_err = msg;
-    return code;
+    return record_error(code, msg);
 }
 
 // Per device, the device address of the scratch array, looked up once with
@@ -222,9 +220,6 @@ extern "C" int mc_energy_noalloc(double L, int n_mol, const uint32_t *dev_q, con
     chk(cudaGetLastError());
     noalloc_poison_kernel<<<1, 32, 0, st>>>(d.err, dev_E_out);
     chk(cudaGetLastError());
-    if (e != cudaSuccess) {
-        g_noalloc_err = std::string("mc_energy_noalloc: ") + cudaGetErrorString(e);
-        return MC_ERR_CUDA;
-    }
+    if (e != cudaSuccess) return noalloc_fail(MC_ERR_CUDA, (std::string("mc_energy_noalloc: ") + cudaGetErrorString(e)).c_str());
     return MC_OK;
 }

@@ -55,3 +55,4 @@ def test_noalloc_rejects_sizes_beyond_its_maximum():
     M = 21846                      # 65538 atoms: one molecule past the limit
     rc = F.mc_energy_noalloc(W.box_length(M), M, buf.data_ptr(), buf.data_ptr(), W.PAPER_POT, buf.data_ptr(), 0)
     assert rc == F.MC_ERR_INVALID_ARG
+    assert "65536 atoms" in F.mc_last_error()
