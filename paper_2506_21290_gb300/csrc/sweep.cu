@@ -1451,18 +1451,25 @@ __device__ void run_cell(const DevState &d, int buf, int colour, const LogArgs &
             int adv = 1;
             if constexpr (W > 1) {
                 gsync<W>(gid);
-                // commit in order up to the first attempt an earlier accepted one may have changed
-                if (wig < nw) {
-                    const bool cl = clashes<W>(G.near, wig, rconf, lane);
-                    if (lane == 0) G.misc[MS_CLASH + wig] = cl;
-                }
-                gsync<W>(gid);
+                // commit in order up to the first attempt an earlier accepted one may
+                // have changed; when no attempt but possibly the last was accepted,
+                // nothing can have changed (every warp reads the same flags)
+                bool any_acc = false;
+#pragma unroll
+                for (int wa = 0; wa < W - 1; ++wa) any_acc |= (wa < nw - 1) && G.near[wa].accept != 0;
                 adv = nw;
-                for (int j = 1; j < nw; ++j)
-                    if (G.misc[MS_CLASH + j]) {
-                        adv = j;
-                        break;
+                if (any_acc) {
+                    if (wig < nw) {
+                        const bool cl = clashes<W>(G.near, wig, rconf, lane);
+                        if (lane == 0) G.misc[MS_CLASH + wig] = cl;
                     }
+                    gsync<W>(gid);
+                    for (int j = 1; j < nw; ++j)
+                        if (G.misc[MS_CLASH + j]) {
+                            adv = j;
+                            break;
+                        }
+                }
             } else {
                 __syncwarp();
             }
