@@ -70,6 +70,32 @@ def parse():
 DEFAULT_SPS = {"tiny-64": 100, "single-1000": 100, "single-8000": 20, "batched-256": 5, "large-64000": 5}
 
 
+def combine_ranks(ms, attempts, pairs, dist=None, device="cpu"):
+    """Whole-job numbers over the ranks of an N-GPU run: the slowest rank's time
+    and the sum of every rank's attempts and pair evaluations (ranks run
+    independent replica sets, so no data-path collective is involved)."""
+    if dist is None:
+        return float(ms), float(attempts), float(pairs)
+    import torch
+    tot = torch.tensor([float(ms), float(attempts), float(pairs)], dtype=torch.float64, device=device)
+    mx = tot.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    sm = tot.clone()
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return float(mx[0]), float(sm[1]), float(sm[2])
+
+
+def config_of(name, wl, sps, precision, warmup, world):
+    """The `config` object of a bench line (both arms)."""
+    return {"workload": name, "molecules": wl["M_total"], "sites": 3 * wl["M_total"], "replicas": wl["replicas"],
+            "T": wl["T"] if wl["replicas"] == 1 else "uniform [0.75, 3.0] per replica",
+            "density": W.RHO, "sweeps_per_step": sps, "precision": precision,
+            "move_mix": "atom translation 0.8 (d=0.1) / flip 0.2",
+            "start": "simple-cubic lattice, random orientations, then %d warm-up steps" % warmup,
+            "l2": "256 MiB buffer written between timed steps",
+            "parallelism": "replicas" if world > 1 else "single GPU"}
+
+
 def make_workload(name, rank=0):
     spec = W.WORKLOADS[name]
     if "R" in spec:
@@ -188,9 +214,10 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "molecules": M0, "T": T, "sweeps_per_step": 1,
-                       "move_mix": "atom 0.8 / flip 0.2"},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "config": config_of(args.workload, wl, args.sweeps_per_step or DEFAULT_SPS[args.workload],
+                                wl["precision"], args.warmup, args.gpus),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                             "note": "each step times one oracle sweep (a bounded sample of the workload)"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -300,15 +327,7 @@ def run_native(args):
     accepts = [sum(s1["accepts"][k] - s0["accepts"][k] for s0, s1 in zip(st0, st1)) for k in range(4)]
     att_k = [sum(s1["attempts"][k] - s0["attempts"][k] for s0, s1 in zip(st0, st1)) for k in range(4)]
     geom = sum(s1["rejected_geometry"] - s0["rejected_geometry"] for s0, s1 in zip(st0, st1))
-    tot = torch.tensor([ms, float(attempts), float(pairs)], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        mx = tot.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        sm = tot.clone()
-        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
-        ms_max, attempts_all, pairs_all = float(mx[0]), float(sm[1]), float(sm[2])
-    else:
-        ms_max, attempts_all, pairs_all = ms, float(attempts), float(pairs)
+    ms_max, attempts_all, pairs_all = combine_ranks(ms, attempts, pairs, dist, "cuda")
     value = attempts_all / (ms_max / 1000.0)
     pair_rate = pairs_all / (ms_max / 1000.0)
 
@@ -374,13 +393,7 @@ def run_native(args):
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if precision == "fp32" else "f64",
         "data": "synthetic",
-        "config": {"workload": args.workload, "molecules": wl["M_total"], "sites": N, "replicas": wl["replicas"],
-                   "T": wl["T"] if wl["replicas"] == 1 else "uniform [0.75, 3.0] per replica",
-                   "density": W.RHO, "sweeps_per_step": sps, "precision": precision,
-                   "move_mix": "atom translation 0.8 (d=0.1) / flip 0.2",
-                   "start": "simple-cubic lattice, random orientations, then %d warm-up steps" % args.warmup,
-                   "l2": "256 MiB buffer written between timed steps",
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "config": config_of(args.workload, wl, sps, precision, args.warmup, world),
         "pair_evals_per_s": pair_rate,
         "pair_evals_fp32_peak_frac": pair_rate * FLOPS_PER_PAIR_EVAL / (peak * 1e12),
         "fp64_recheck_rate": rechecks / max(attempts, 1),
