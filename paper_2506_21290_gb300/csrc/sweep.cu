@@ -1,39 +1,42 @@
 // Checkerboard Metropolis sweep (arXiv 2506.21290 Sec. II.B on a cell grid).
 //
 // A group of W warps (W = 1, 2 or 4) owns one active cell of the current
-// colour.  It stages the atoms of the cell and of its neighbour cells (27, or
-// the 8 distinct cells when n_c = 2) in shared memory and draws the random
-// numbers of its attempts up front (Philox is counter-based: the draws do not
-// depend on the state).  The cell's n attempts then run in rounds: in a round
-// the W warps evaluate W consecutive attempts against the same state, each
-// warp one attempt, and one thread commits them in order.  The commit stops at
-// the first attempt that an earlier accepted attempt of the round could have
-// influenced: same molecule, or an atom of the earlier move (old or new
-// position) within 1.01 times the largest WCA cutoff of an atom of the later
-// one.  Interactions between different molecules are WCA only, so an attempt
-// that passes this test has exactly the Delta E, decision and log entry it
-// would have had after the earlier commit; the uncommitted attempts are
-// evaluated again in the next round.  The chain is therefore the sequential
-// one, for every W.
+// colour.  It stages the raw records of the cell and of its neighbour cells
+// (27, or the 8 distinct cells when n_c = 2) in shared memory, one bulk copy
+// per cell, and loads the draws of its attempts, which the cell-list build
+// decoded beforehand (Philox is counter-based: the draws do not depend on the
+// state).  The cell's n attempts then run in rounds: in a round the W warps
+// evaluate W consecutive attempts against the same state, one attempt per
+// warp.  The attempts commit in order up to the first one that an earlier
+// accepted attempt of the round could have influenced: same molecule, or an
+// atom of the earlier move (old or new position) within 1.01 times the largest
+// WCA cutoff of an atom of the later one.  Interactions between different
+// molecules are WCA only, so an attempt that passes this test has exactly the
+// Delta E, decision and log entry it would have had after the earlier commit;
+// the uncommitted attempts are evaluated again in the next round.  The chain is
+// therefore the sequential one, for every W.
 //
-// FP32 mode, one attempt by one warp:
-//   1. candidate pass: each lane takes pairs of candidates from the cell-local
-//      structure-of-arrays coordinates and evaluates old and new squared
-//      distances with packed f32x2 arithmetic (the new one as
-//      r'^2 = r^2 - 2 d.delta + |delta|^2); candidates inside the screening
-//      radius (r^2 < 1.01 x the largest WCA cutoff squared), or in the same
-//      molecule, are queued in ballot order.  Both modes run this pass.
+// One attempt, one warp (FP32 mode):
+//   1. screen: each lane takes one candidate per 32-candidate step; the exact
+//      int32 minimum-image differences to the moved atom's old position,
+//      converted to FP32, give r^2, and the new one follows as
+//      r'^2 = r^2 - 2 d.e + |e|^2; candidates inside the screening radius
+//      (r^2 < 1.01 x the largest WCA cutoff squared), or in the same molecule,
+//      are queued in ballot order.  Both modes run this pass.
 //   2. interaction pass over the queue: WCA (Eq. 1) and FENE (Eq. 2), old and
-//      new, in FP32, each with a magnitude that bounds its rounding error.
-//   3. decision: |dE32 - thr32| against gap * sum(magnitudes) plus the error
-//      bound of the FP32 threshold -T ln u.  Outside that band the FP32
+//      new, in FP32 from the exact int32 differences (one rounding per axis),
+//      each term with a magnitude m that bounds its rounding error.
+//   3. decision: |dE32 - thr32| against gap * sum(m) (gap = 1e-5 by default)
+//      plus the error bound of the FP32 threshold -T ln u.  The FP32 Delta E is
+//      within 6.3e-6 sum(m) of the exact one (distances within ~9 units of
+//      2^-24, each term's sensitivity to them at most 6 m, its own evaluation
+//      ~31 units, the sums ~21 units), so outside that band the FP32
 //      comparison agrees with the FP64 one; inside it (or near a FENE
-//      divergence, or on a non-finite value) the warp recomputes Delta E and
-//      the threshold in FP64, in the reference order, and decides on those.
-// The FP32 error of a pair term is at most a few 1e-6 of its magnitude
-// 4 eps s^12 + 4 eps s^6 + eps (FENE: K eps (|ln(1-x)| + x/(1-x))): positions
-// are cell-local (|x| < 1.5 cells), so r^2 carries ~5e-7 relative error, s^6 and
-// s^12 ~2e-6 and ~4e-6; gap = 1e-4 leaves a factor of >= 10.
+//      divergence, or when the queue overflowed) the warp recomputes Delta E
+//      and the threshold in FP64, in the reference order, and decides on them.
+// No step of the hot path branches per lane: lanes past the staged atoms read
+// a padding record, discarded queue writes go to a spare slot, and terms are
+// masked instead of skipped.
 //
 // FP64 mode: every Delta E is the FP64 ordered sum (moved atom ascending, then
 // partner index ascending) of the nonzero pair terms, each operation unfused
@@ -54,10 +57,9 @@ constexpr int TERM_CAP = 128;       // nonzero FP64 terms of one move
 constexpr int QW = 64;              // interaction queue entries per warp
 constexpr int BLOCK = 128;          // threads per block (all W)
 constexpr unsigned FULL = 0xffffffffu;
-constexpr float FAR = 1.0e18f;      // coordinate of the padding candidates (fixed-point units)
 constexpr int PADS = kPadSlots;     // padding candidates staged after the K atoms
 constexpr int PAD_W = kPadWord;     // their record word: type 0, a molecule no atom has
-constexpr int SCREEN_U = 4;         // 64-candidate steps per screening block
+constexpr int SCREEN_U = 8;         // 32-candidate steps per screening block
 
 // ---------------------------------------------------------------------------
 // packed FP32 pairs (f32x2, sm_100 and later)
@@ -98,45 +100,24 @@ struct Q3 {
 };
 
 // ---------------------------------------------------------------------------
-// Cell-local coordinates.  A staged atom's position relative to the cell
-// centre P is the int32 X = q - P in fixed-point units (|X| < 2^31 when
-// n_c >= 4).  It is kept as X = H + l with H a multiple of 256 and 0 <= l < 256:
-// H is exact in FP32 (at most 23 significant bits), and so is the difference
-// of two H (a multiple of 256 below 2^32), so a distance built from H
-// differences only carries the rounding of its own squares and sums.  The low
-// bytes l are added back for the pairs that enter Delta E.
+// Distances from the raw fixed-point records.  The int32 difference of two
+// 32-bit fixed-point coordinates is their minimum-image difference in units of
+// the quantum h = L / 2^32, exactly, for any n_c.  Converting it to FP32 rounds
+// once (relative 2^-24), so a squared distance carries only that rounding and
+// the rounding of its squares and sums; no absolute error grows with the
+// distance from any origin.
 // ---------------------------------------------------------------------------
-struct HiLo {
-    float x, y, z;   // H per axis
-    int lo;          // l per axis, packed x | y << 8 | z << 16
-};
+__device__ __forceinline__ float dq(uint32_t a, uint32_t b) { return (float)(int)(a - b); }
 
-__device__ __forceinline__ HiLo make_hilo(int X, int Y, int Z)
+// squared distance of record r to position b, fixed-point units squared
+__device__ __forceinline__ float r2_q(const int4 &r, const Q3 &b)
 {
-    HiLo r;
-    r.x = (float)(X & ~255);
-    r.y = (float)(Y & ~255);
-    r.z = (float)(Z & ~255);
-    r.lo = (X & 255) | ((Y & 255) << 8) | ((Z & 255) << 16);
-    return r;
+    const float x = dq((uint32_t)r.x, b.x), y = dq((uint32_t)r.y, b.y), z = dq((uint32_t)r.z, b.z);
+    return fmaf(x, x, fmaf(y, y, z * z));
 }
 
-// byte b of a packed word as the float 2^23 + b (integer OR, no conversion):
-// the difference of two such values is the exact difference of the bytes
-__device__ __forceinline__ float lo_f(int lo, int sh) { return __int_as_float(0x4B000000 | ((lo >> sh) & 255)); }
-
-// squared distance in fixed-point units squared: exact H differences plus exact
-// l differences, one rounding per axis, then the squares and sums
-__device__ __forceinline__ float r2_acc(float X, float Y, float Z, int lo, const HiLo &o)
-{
-    const float ex = (X - o.x) + (lo_f(lo, 0) - lo_f(o.lo, 0));
-    const float ey = (Y - o.y) + (lo_f(lo, 8) - lo_f(o.lo, 8));
-    const float ez = (Z - o.z) + (lo_f(lo, 16) - lo_f(o.lo, 16));
-    return fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-}
-
-// squared distance from raw fixed-point records (any n_c): int32 differences
-// (the minimum image), converted and scaled by h
+// squared distance in sigma units from raw fixed-point positions (one lane,
+// intramolecular pairs of a rotation)
 __device__ __forceinline__ float r2_int32f(const int4 &r, const Q3 b, float hf)
 {
     const float dx = (float)(int)((uint32_t)r.x - b.x) * hf;
@@ -144,6 +125,11 @@ __device__ __forceinline__ float r2_int32f(const int4 &r, const Q3 b, float hf)
     const float dz = (float)(int)((uint32_t)r.z - b.z) * hf;
     return fmaf(dx, dx, fmaf(dy, dy, dz * dz));
 }
+
+// a moved atom's position relative to the cell centre P, for the conflict test
+struct PosH {
+    float x, y, z;
+};
 
 // ---------------------------------------------------------------------------
 // shared memory
@@ -206,7 +192,6 @@ struct Res {
     int status, accept, flags, mvt, nmv, site, mol;
     int ks[3], t3n[3];
     uint32_t qn[3][3];
-    HiLo hn[3];                 // new positions of the moved atoms, split as staged
     float dE32;                 // FP32 mode: the FP32 Delta E
     float scale;                // FP32 mode: sum of the term magnitudes
     double dE64;                // the FP64 Delta E (FP64 mode, or an FP32-mode recheck), else NaN
@@ -216,7 +201,7 @@ struct Res {
 // what the conflict test of the later attempts of a round reads (W > 1)
 struct Near {
     int accept, mol, nat, pad;
-    float px[6], py[6], pz[6];  // H of the move's atoms (old and new)
+    float px[6], py[6], pz[6];  // the move's atoms (old and new) relative to the cell centre, fixed-point units
 };
 
 // attempt counts of one warp over one cell
@@ -228,10 +213,8 @@ struct Tally {
 };
 
 struct Group {
-    float *sx, *sy, *sz;        // [cap] H of the staged atoms (fixed-point units)
-    int *sl;                    // [cap] their packed low bytes
-    int *sw;                    // [cap] record words
-    int4 *rec;                  // [cap] raw records {qx, qy, qz, w} of the neighbourhood, own cell first
+    int4 *rec;                  // [cap] raw records {qx, qy, qz, w} of the neighbourhood, own cell first,
+                                //       then kPadSlots padding records
     int4 *orig;                 // [own_cap] the own cell as staged (periodic images at write-back)
     uint64_t *mbar;             // completion barrier of the bulk copies that stage rec
     uint32_t *rnd;              // [32 * 8] random words of a chunk of attempts
@@ -258,7 +241,7 @@ __host__ __device__ inline size_t warp_scr_bytes()
 
 __host__ __device__ inline size_t group_bytes(int cap, int own_cap, int W)
 {
-    return 5 * al16(sizeof(float) * cap) + al16(sizeof(int4) * cap) + al16(sizeof(int4) * own_cap) + 16 +
+    return al16(sizeof(int4) * cap) + al16(sizeof(int4) * own_cap) + 16 +
            al16(sizeof(uint32_t) * 256) +
            al16(sizeof(double) * 32) + al16(sizeof(float) * 32) + 3 * al16(sizeof(int) * 32) +
            al16(sizeof(Near) * W) + al16(sizeof(Tally) * W) + (size_t)W * warp_scr_bytes();
@@ -273,11 +256,6 @@ __device__ inline Group carve(unsigned char *base, int cap, int own_cap, int W)
         o += al16(bytes);
         return p;
     };
-    s.sx = (float *)take(sizeof(float) * cap);
-    s.sy = (float *)take(sizeof(float) * cap);
-    s.sz = (float *)take(sizeof(float) * cap);
-    s.sl = (int *)take(sizeof(int) * cap);
-    s.sw = (int *)take(sizeof(int) * cap);
     s.rec = (int4 *)take(sizeof(int4) * cap);
     s.orig = (int4 *)take(sizeof(int4) * own_cap);
     s.mbar = (uint64_t *)take(16);
@@ -327,22 +305,11 @@ __device__ __forceinline__ float warp_sum_f(float v)
     return v;
 }
 
-// Staged records: the own cell lives in shared memory (it changes during the
-// phase); neighbour cells are read from shared memory when the whole
-// neighbourhood is staged raw, else from global memory (they do not change).
+// The staged raw records of the neighbourhood (shared memory), as the FP64
+// ordered sum reads them.
 struct RecView {
     const int4 *smem;
-    bool full;
-    int n;
-    const int4 *gsrc;
-    const int *cstart, *coff;
-    int ns;
-    __device__ int4 at(int c) const
-    {
-        if (full || c < n) return smem[c];
-        const int k = find_segment(coff, ns, c);
-        return gsrc[cstart[k] + (c - coff[k])];
-    }
+    __device__ int4 at(int c) const { return smem[c]; }
 };
 
 // A proposed move, as the FP64 ordered sum needs it.
@@ -511,161 +478,92 @@ __device__ __noinline__ void rotate_molecule(const uint32_t (*q)[3], uint32_t (*
 // ---------------------------------------------------------------------------
 // Candidate screens: queue every partner within the screening radius of an
 // old or new position of a moved atom (and, for single-atom moves and flips,
-// every atom of the molecule).  The loads and the arithmetic of U steps of 64
-// candidates are issued before any queue store, and the queue is filled in
-// ballot order afterwards; entries past QW are counted but not stored.
+// every atom of the molecule).  A lane takes one candidate per 32-candidate
+// step; the loads and arithmetic of SCREEN_U steps are issued before any queue
+// store, and the queue is filled in ballot order afterwards.  Lanes past the
+// K staged atoms read the first padding record (no molecule, never within
+// reach), so no lane branches; entries past QW are counted but not stored.
 // ---------------------------------------------------------------------------
 
-// append the hits of one 64-candidate step (candidate c = base + 2 lane for
-// bit b0, c + 1 for b1) in ballot order.  Every lane stores: lanes without a
-// hit, and hits past QW, write the discard slot, so the warp never diverges.
-__device__ __forceinline__ void queue_step(const WarpScr &S, int lane, int &qlen, unsigned b0, unsigned b1, int c)
+// append the hits of one 32-candidate step (candidate c = base + lane) in
+// ballot order; lanes without a hit, and hits past QW, write the discard slot
+__device__ __forceinline__ void queue_step(const WarpScr &S, int lane, int &qlen, unsigned b, int c)
 {
     const unsigned lt = (1u << lane) - 1u;
-    const int e0 = ((b0 >> lane) & 1u) ? min(qlen + __popc(b0 & lt), QW) : QW;
-    const int e1 = ((b1 >> lane) & 1u) ? min(qlen + __popc(b0) + __popc(b1 & lt), QW) : QW;
-    S.qc[e0] = c;
-    S.qc[e1] = c + 1;
-    qlen += __popc(b0) + __popc(b1);
+    const int e = ((b >> lane) & 1u) ? min(qlen + __popc(b & lt), QW) : QW;
+    S.qc[e] = c;
+    qlen += __popc(b);
 }
 
-// Atom translation from o to nn (H parts): the old distance, and the new one
-// as r'^2 = r^2 - 2 d.e + |d|^2, in packed FP32 pairs.
-__device__ __forceinline__ int screen_atom(const Group &G, const WarpScr &S, int K, int lane, const HiLo &o,
-                                           const HiLo &nn, int wi, float r2q)
+// Atom translation from qo to qo + e: the old distance from the exact int32
+// difference, the new one as r'^2 = r^2 - 2 d.e + |e|^2 (fixed-point units).
+__device__ __forceinline__ int screen_atom(const Group &G, const WarpScr &S, int K, int lane, const Q3 &qo,
+                                           const Q3 &qn, int wi, float r2q)
 {
-    const float dx = nn.x - o.x, dy = nn.y - o.y, dz = nn.z - o.z;   // exact
-    const f2_t nxo = pk(-o.x, -o.x), nyo = pk(-o.y, -o.y), nzo = pk(-o.z, -o.z);
-    const f2_t mx = pk(-2.f * dx, -2.f * dx), my = pk(-2.f * dy, -2.f * dy), mz = pk(-2.f * dz, -2.f * dz);
-    const float dd = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    const f2_t d2 = pk(dd, dd);
-    const int cpad = (K + 1) & ~1;   // an even index whose pair is padding
+    const float ex = dq(qn.x, qo.x), ey = dq(qn.y, qo.y), ez = dq(qn.z, qo.z);
+    const float mx = -2.f * ex, my = -2.f * ey, mz = -2.f * ez;
+    const float ee = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
     int qlen = 0;
-    for (int base = 0; base < K; base += 64 * SCREEN_U) {
-        unsigned b0[SCREEN_U], b1[SCREEN_U];
+    for (int base = 0; base < K; base += 32 * SCREEN_U) {
+        unsigned b[SCREEN_U];
 #pragma unroll
         for (int u = 0; u < SCREEN_U; ++u) {
-            const int c = base + 64 * u + 2 * lane;
-            const int cl = c < K ? c : cpad;   // past the end: the padding pair (far, no molecule)
-            const f2_t X = *(const f2_t *)(G.sx + cl);
-            const f2_t Y = *(const f2_t *)(G.sy + cl);
-            const f2_t Z = *(const f2_t *)(G.sz + cl);
-            const int2 ww = *(const int2 *)(G.sw + cl);
-            const f2_t ex = add2(X, nxo), ey = add2(Y, nyo), ez = add2(Z, nzo);
-            const f2_t r2o = fma2(ez, ez, fma2(ey, ey, mul2(ex, ex)));
-            const f2_t r2n = fma2(ez, mz, fma2(ey, my, fma2(ex, mx, add2(r2o, d2))));
-            float a0, a1, n0, n1;
-            upk(r2o, a0, a1);
-            upk(r2n, n0, n1);
-            const bool p0 = (fminf(a0, n0) < r2q) | ((ww.x ^ wi) < 16);
-            const bool p1 = (fminf(a1, n1) < r2q) | ((ww.y ^ wi) < 16);
-            b0[u] = __ballot_sync(FULL, p0);
-            b1[u] = __ballot_sync(FULL, p1);
+            const int c = base + 32 * u + lane;
+            const int4 r = G.rec[c < K ? c : K];
+            const float dx = dq((uint32_t)r.x, qo.x), dy = dq((uint32_t)r.y, qo.y), dz = dq((uint32_t)r.z, qo.z);
+            const float r2o = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+            const float r2n = fmaf(dz, mz, fmaf(dy, my, fmaf(dx, mx, r2o + ee)));
+            const bool near = (fminf(r2o, r2n) < r2q) & (r.w != PAD_W);
+            b[u] = __ballot_sync(FULL, near | ((r.w ^ wi) < 16));
         }
 #pragma unroll
-        for (int u = 0; u < SCREEN_U; ++u) queue_step(S, lane, qlen, b0[u], b1[u], base + 64 * u + 2 * lane);
+        for (int u = 0; u < SCREEN_U; ++u) queue_step(S, lane, qlen, b[u], base + 32 * u + lane);
     }
     return qlen;
 }
 
 // Flip: distance of every candidate to the two atoms whose types swap.
-__device__ __forceinline__ int screen_flip(const Group &G, const WarpScr &S, int K, int lane, const HiLo &hp,
-                                           const HiLo &hq, int wi, float r2q)
+__device__ __forceinline__ int screen_flip(const Group &G, const WarpScr &S, int K, int lane, const Q3 &qp,
+                                           const Q3 &qq, int wi, float r2q)
 {
-    const f2_t npx = pk(-hp.x, -hp.x), npy = pk(-hp.y, -hp.y), npz = pk(-hp.z, -hp.z);
-    const f2_t nqx = pk(-hq.x, -hq.x), nqy = pk(-hq.y, -hq.y), nqz = pk(-hq.z, -hq.z);
-    const int cpad = (K + 1) & ~1;
     int qlen = 0;
-    for (int base = 0; base < K; base += 64 * SCREEN_U) {
-        unsigned b0[SCREEN_U], b1[SCREEN_U];
+    for (int base = 0; base < K; base += 32 * SCREEN_U) {
+        unsigned b[SCREEN_U];
 #pragma unroll
         for (int u = 0; u < SCREEN_U; ++u) {
-            const int c = base + 64 * u + 2 * lane;
-            const int cl = c < K ? c : cpad;
-            const f2_t X = *(const f2_t *)(G.sx + cl);
-            const f2_t Y = *(const f2_t *)(G.sy + cl);
-            const f2_t Z = *(const f2_t *)(G.sz + cl);
-            const int2 ww = *(const int2 *)(G.sw + cl);
-            f2_t ex = add2(X, npx), ey = add2(Y, npy), ez = add2(Z, npz);
-            const f2_t rp = fma2(ez, ez, fma2(ey, ey, mul2(ex, ex)));
-            ex = add2(X, nqx);
-            ey = add2(Y, nqy);
-            ez = add2(Z, nqz);
-            const f2_t rq = fma2(ez, ez, fma2(ey, ey, mul2(ex, ex)));
-            float a0, a1, n0, n1;
-            upk(rp, a0, a1);
-            upk(rq, n0, n1);
-            const bool p0 = (fminf(a0, n0) < r2q) | ((ww.x ^ wi) < 16);
-            const bool p1 = (fminf(a1, n1) < r2q) | ((ww.y ^ wi) < 16);
-            b0[u] = __ballot_sync(FULL, p0);
-            b1[u] = __ballot_sync(FULL, p1);
+            const int c = base + 32 * u + lane;
+            const int4 r = G.rec[c < K ? c : K];
+            const bool near = (fminf(r2_q(r, qp), r2_q(r, qq)) < r2q) & (r.w != PAD_W);
+            b[u] = __ballot_sync(FULL, near | ((r.w ^ wi) < 16));
         }
 #pragma unroll
-        for (int u = 0; u < SCREEN_U; ++u) queue_step(S, lane, qlen, b0[u], b1[u], base + 64 * u + 2 * lane);
+        for (int u = 0; u < SCREEN_U; ++u) queue_step(S, lane, qlen, b[u], base + 32 * u + lane);
     }
     return qlen;
 }
 
 // Rigid molecule move: the three atoms, old and new (molecule partners are
 // not queued: their distances do not change).
-__device__ __noinline__ int screen_mol(const Group G, const WarpScr S, int K, int lane, const HiLo *ho,
-                                       const HiLo *hn, int wi, float r2q)
+__device__ __noinline__ int screen_mol(const Group G, const WarpScr S, int K, int lane, const Q3 *qo, const Q3 *qn,
+                                       int wi, float r2q)
 {
     int qlen = 0;
-    for (int base = 0; base < K; base += 64) {
-        bool pp[2] = {false, false};
-#pragma unroll
-        for (int hh = 0; hh < 2; ++hh) {
-            const int c = base + 2 * lane + hh;
-            if (c < K) {
-                const float x = G.sx[c], y = G.sy[c], z = G.sz[c];
-                float mn = 3.0e38f;
-#pragma unroll
-                for (int s = 0; s < 3; ++s) {
-                    float ex = x - ho[s].x, ey = y - ho[s].y, ez = z - ho[s].z;
-                    mn = fminf(mn, fmaf(ex, ex, fmaf(ey, ey, ez * ez)));
-                    ex = x - hn[s].x;
-                    ey = y - hn[s].y;
-                    ez = z - hn[s].z;
-                    mn = fminf(mn, fmaf(ex, ex, fmaf(ey, ey, ez * ez)));
-                }
-                pp[hh] = (mn < r2q) && ((G.sw[c] ^ wi) >= 16);
-            }
-        }
-        queue_step(S, lane, qlen, __ballot_sync(FULL, pp[0]), __ballot_sync(FULL, pp[1]), base + 2 * lane);
-    }
-    return qlen;
-}
-
-// n_c = 2 boxes: distances from the raw records (the neighbourhood wraps onto
-// itself, so each pair takes its own minimum image).  npos positions; for a
-// rigid move (mol_move) the molecule is excluded, else always included.
-__device__ __noinline__ int screen_raw(const Group G, const WarpScr S, int K, int lane, const Q3 *pos, int npos,
-                                       int wi, bool mol_move, float hf, float r2q)
-{
-    int qlen = 0;
-    for (int base = 0; base < K; base += 64) {
-        bool pp[2] = {false, false};
-#pragma unroll
-        for (int hh = 0; hh < 2; ++hh) {
-            const int c = base + 2 * lane + hh;
-            if (c < K) {
-                const int4 r = G.rec[c];
-                float mn = 3.0e38f;
-                for (int s = 0; s < npos; ++s) mn = fminf(mn, r2_int32f(r, pos[s], hf));
-                const bool same = (r.w ^ wi) < 16;
-                pp[hh] = mol_move ? ((mn < r2q) && !same) : ((mn < r2q) || same);
-            }
-        }
-        queue_step(S, lane, qlen, __ballot_sync(FULL, pp[0]), __ballot_sync(FULL, pp[1]), base + 2 * lane);
+    for (int base = 0; base < K; base += 32) {
+        const int c = base + lane;
+        const int4 r = G.rec[c < K ? c : K];
+        float mn = 3.0e38f;
+        for (int s = 0; s < 3; ++s) mn = fminf(mn, fminf(r2_q(r, qo[s]), r2_q(r, qn[s])));
+        const bool hit = (mn < r2q) && r.w != PAD_W && ((r.w ^ wi) >= 16);
+        queue_step(S, lane, qlen, __ballot_sync(FULL, hit), c);
     }
     return qlen;
 }
 
 // ---------------------------------------------------------------------------
 // FP32 interaction passes over the queue (each lane takes entries lane and
-// lane + 32): partial (dE, mag, guard) per lane.  Distances are recomputed
-// accurately from the staged coordinates (H and l, or the raw records).
+// lane + 32): partial (dE, mag, guard) per lane.  Distances come from the
+// exact int32 differences of the raw records, converted once per axis (and
+// scaled by h^2): at most about 7 units of 2^-24 relative error in r^2.
 // ---------------------------------------------------------------------------
 struct Acc32 {
     float dE, mag;
@@ -721,63 +619,33 @@ __device__ __forceinline__ void fene_m(const ModelDev &md, float r2, int ab, flo
     a.mag = fmaf(f, md.kef * (fabsf(l) + __fdividef(xs, y) + 1.0f), a.mag);
 }
 
-// one queued candidate as the interaction passes need it
-struct Cand {
-    float X, Y, Z;
-    int lo;
-    int4 r;
-    int w;
-};
-
-__device__ __forceinline__ Cand load_cand(const Group &G, bool raw, int c)
+// squared distance in sigma units of queued record r to position q; a padding
+// record is beyond every cutoff
+__device__ __forceinline__ float cand_r2(const int4 &r, const Q3 &q, float h2)
 {
-    Cand d;
-    if (raw) {
-        d.r = G.rec[c];
-        d.w = d.r.w;
-        d.X = d.Y = d.Z = 0.f;
-        d.lo = 0;
-    } else {
-        d.X = G.sx[c];
-        d.Y = G.sy[c];
-        d.Z = G.sz[c];
-        d.lo = G.sl[c];
-        d.w = G.sw[c];
-        d.r = make_int4(0, 0, 0, 0);
-    }
-    return d;
+    return r.w == PAD_W ? 1.0e30f : r2_q(r, q) * h2;
 }
 
-// squared distance (sigma units) of a candidate to a moved atom's position;
-// a padding candidate is beyond every cutoff
-__device__ __forceinline__ float cand_r2(const Cand &d, bool raw, const HiLo &h, const Q3 &q, float hf, float h2)
-{
-    const float r2 = raw ? r2_int32f(d.r, q, hf) : r2_acc(d.X, d.Y, d.Z, d.lo, h) * h2;
-    return d.w == PAD_W ? 1.0e30f : r2;
-}
-
-// Entry e of the queue, or the padding candidate cpad when e is past the
-// queue or names one of the moved atoms.
-__device__ __forceinline__ int queued(const WarpScr &S, int e, int nq, int cpad, int k0, int k1)
+// Entry e of the queue, or the padding record K when e is past the queue or
+// names one of the moved atoms.
+__device__ __forceinline__ int queued(const WarpScr &S, int e, int nq, int K, int k0, int k1)
 {
     const int cq = S.qc[e];   // e < QW: inside the queue array
-    return (e < nq && cq != k0 && cq != k1) ? cq : cpad;
+    return (e < nq && cq != k0 && cq != k1) ? cq : K;
 }
 
 __device__ __forceinline__ Acc32 inter_atom(const Group &G, const WarpScr &S, int nq, int lane, const ModelDev &md,
-                                            bool raw, int k, int cpad, int wi, int ti, const HiLo &ho, const HiLo &hn,
-                                            const Q3 &qo, const Q3 &qn, float hf, float h2)
+                                            int K, int k, int wi, int ti, const Q3 &qo, const Q3 &qn, float h2)
 {
     Acc32 a{0.f, 0.f, 0};
     const int slots = nq > 32 ? 2 : 1;   // warp-uniform
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
         if (s < slots) {
-            const int c = queued(S, lane + 32 * s, nq, cpad, k, k);
-            const Cand d = load_cand(G, raw, c);
-            const int ab = 3 * ti + rec_type(d.w);
-            const bool bonded = (d.w ^ wi) < 16;
-            const float r2o = cand_r2(d, raw, ho, qo, hf, h2), r2n = cand_r2(d, raw, hn, qn, hf, h2);
+            const int4 r = G.rec[queued(S, lane + 32 * s, nq, K, k, k)];
+            const int ab = 3 * ti + rec_type(r.w);
+            const bool bonded = (r.w ^ wi) < 16;
+            const float r2o = cand_r2(r, qo, h2), r2n = cand_r2(r, qn, h2);
             wca_m(md, r2o, ab, -1.f, a);
             wca_m(md, r2n, ab, 1.f, a);
             fene_m(md, r2o, ab, -1.f, bonded, a);
@@ -788,20 +656,18 @@ __device__ __forceinline__ Acc32 inter_atom(const Group &G, const WarpScr &S, in
 }
 
 __device__ __forceinline__ Acc32 inter_flip(const Group &G, const WarpScr &S, int nq, int lane, const ModelDev &md,
-                                            bool raw, int kp, int kq, int cpad, int wi, int tp, int tq,
-                                            const HiLo &hp, const HiLo &hq, const Q3 &qp, const Q3 &qq, float hf,
-                                            float h2)
+                                            int K, int kp, int kq, int wi, int tp, int tq, const Q3 &qp,
+                                            const Q3 &qq, float h2)
 {
     Acc32 a{0.f, 0.f, 0};
     const int slots = nq > 32 ? 2 : 1;
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
         if (s < slots) {
-            const int c = queued(S, lane + 32 * s, nq, cpad, kp, kq);
-            const Cand d = load_cand(G, raw, c);
-            const int tj = rec_type(d.w);
-            const bool bonded = (d.w ^ wi) < 16;
-            const float rp = cand_r2(d, raw, hp, qp, hf, h2), rq = cand_r2(d, raw, hq, qq, hf, h2);
+            const int4 r = G.rec[queued(S, lane + 32 * s, nq, K, kp, kq)];
+            const int tj = rec_type(r.w);
+            const bool bonded = (r.w ^ wi) < 16;
+            const float rp = cand_r2(r, qp, h2), rq = cand_r2(r, qq, h2);
             // atom p: type tp -> tq; atom q: type tq -> tp
             wca_m(md, rp, 3 * tp + tj, -1.f, a);
             wca_m(md, rp, 3 * tq + tj, 1.f, a);
@@ -816,21 +682,17 @@ __device__ __forceinline__ Acc32 inter_flip(const Group &G, const WarpScr &S, in
     return a;
 }
 
-__device__ __noinline__ Acc32 inter_mol(const Group G, const WarpScr S, int nq, int lane, const ModelDev &md,
-                                        bool raw, const int *t3, const HiLo *ho, const HiLo *hn, const Q3 *qo,
-                                        const Q3 *qn, float hf, float h2)
+__device__ __noinline__ Acc32 inter_mol(const Group G, const WarpScr S, int nq, int lane, const ModelDev &md, int K,
+                                        const int *t3, const Q3 *qo, const Q3 *qn, float h2)
 {
     Acc32 a{0.f, 0.f, 0};
     for (int s = 0; s < 2; ++s) {
-        const int e = lane + 32 * s;
-        if (e < nq) {
-            const Cand d = load_cand(G, raw, S.qc[e]);
-            const int tj = rec_type(d.w);
-            for (int m = 0; m < 3; ++m) {
-                const int ab = 3 * t3[m] + tj;
-                add_wca(md, cand_r2(d, raw, ho[m], qo[m], hf, h2), ab, -1.f, a);
-                add_wca(md, cand_r2(d, raw, hn[m], qn[m], hf, h2), ab, 1.f, a);
-            }
+        const int4 r = G.rec[queued(S, lane + 32 * s, nq, K, -1, -1)];
+        const int tj = rec_type(r.w);
+        for (int m = 0; m < 3; ++m) {
+            const int ab = 3 * t3[m] + tj;
+            wca_m(md, cand_r2(r, qo[m], h2), ab, -1.f, a);
+            wca_m(md, cand_r2(r, qn[m], h2), ab, 1.f, a);
         }
     }
     return a;
@@ -864,20 +726,19 @@ struct CellCtx {
     const MixDev *mx;
     RecView rv;
     int K, n, cellL, nc;
-    bool raw;               // n_c = 2: distances from the raw records
-    uint32_t P[3];          // cell centre (fixed point): origin of the cell-local frame
+    uint32_t P[3];          // cell centre (fixed point): origin of the conflict test's frame
     uint32_t shift[3];
     double h, inv_h, T64;
     float hf, h2f;          // h and h^2 in FP32
     float pre_r2;           // screening radius squared (sigma units): 1.01 x the largest WCA cutoff squared
-    float r2q;              // the same in the units of the screens (fixed-point units squared unless raw)
+    float r2q;              // the same in fixed-point units squared (the screens' units)
     float gap, T32;
     int *err;
 };
 
-__device__ __forceinline__ HiLo hilo_of(const CellCtx &c, const Q3 &q)
+__device__ __forceinline__ PosH local_of(const CellCtx &c, const Q3 &q)
 {
-    return make_hilo((int)(q.x - c.P[0]), (int)(q.y - c.P[1]), (int)(q.z - c.P[2]));
+    return PosH{dq(q.x, c.P[0]), dq(q.y, c.P[1]), dq(q.z, c.P[2])};
 }
 
 // Evaluate attempt `jr` of the current chunk (one warp, state read-only) and
@@ -915,7 +776,7 @@ __device__ Res evaluate(const CellCtx &cx, const Group &G, const WarpScr &S, Nea
         // the molecule's atoms in the own cell
         int k0 = -1, k1 = -1, k2 = -1;
         for (int j = 0; j < n; ++j) {
-            const int wj = G.sw[j];
+            const int wj = G.rec[j].w;
             if (rec_mol(wj) == mol) {
                 const int sl = rec_slot(wj);
                 if (sl == 0) k0 = j;
@@ -981,13 +842,6 @@ __device__ Res evaluate(const CellCtx &cx, const Group &G, const WarpScr &S, Nea
             }
         }
     }
-    // the moved atoms in the cell-local frame, old and new
-    HiLo ho[3], hn[3];
-#pragma unroll
-    for (int s = 0; s < 3; ++s) {
-        ho[s] = hilo_of(cx, qo[s]);
-        hn[s] = hilo_of(cx, qn[s]);
-    }
 
     // the FP64 ordered sum of this move and its decision (-1: bond break)
     auto exact = [&](double thr, int nq) {
@@ -998,7 +852,7 @@ __device__ Res evaluate(const CellCtx &cx, const Group &G, const WarpScr &S, Nea
         mv.intra = mvt == MC_MOVE_MOL_ROT;
 #pragma unroll
         for (int s = 0; s < 3; ++s) {
-            mv.site[s] = s < nmv ? rec_site(G.sw[ks[s]]) : -1;
+            mv.site[s] = s < nmv ? rec_site(G.rec[ks[s]].w) : -1;
             mv.to[s] = t3o[s];
             mv.tn[s] = t3n[s];
             mv.qo[s][0] = qo[s].x;
@@ -1016,28 +870,17 @@ __device__ Res evaluate(const CellCtx &cx, const Group &G, const WarpScr &S, Nea
 
     if (status == MC_ST_EVALUATED) {
         int qlen;
-        if (cx.raw) {
-            const Q3 pos[6] = {qo[0], qo[1], qo[2], qn[0], qn[1], qn[2]};
-            if (mvt == MC_MOVE_ATOM) {
-                const Q3 p2[2] = {qo[0], qn[0]};
-                qlen = screen_raw(G, S, K, lane, p2, 2, wi, false, cx.hf, cx.r2q);
-            } else if (mvt == MC_MOVE_FLIP) {
-                qlen = screen_raw(G, S, K, lane, pos, 2, wi, false, cx.hf, cx.r2q);
-            } else {
-                qlen = screen_raw(G, S, K, lane, pos, 6, wi, true, cx.hf, cx.r2q);
-            }
-        } else if (mvt == MC_MOVE_ATOM) {
-            qlen = screen_atom(G, S, K, lane, ho[0], hn[0], wi, cx.r2q);
+        if (mvt == MC_MOVE_ATOM) {
+            qlen = screen_atom(G, S, K, lane, qo[0], qn[0], wi, cx.r2q);
         } else if (mvt == MC_MOVE_FLIP) {
-            qlen = screen_flip(G, S, K, lane, ho[0], ho[1], wi, cx.r2q);
+            qlen = screen_flip(G, S, K, lane, qo[0], qo[1], wi, cx.r2q);
         } else {
-            const HiLo a[3] = {ho[0], ho[1], ho[2]}, b[3] = {hn[0], hn[1], hn[2]};
+            const Q3 a[3] = {qo[0], qo[1], qo[2]}, b[3] = {qn[0], qn[1], qn[2]};
             qlen = screen_mol(G, S, K, lane, a, b, wi, cx.r2q);
         }
         __syncwarp();
         const int nq = min(qlen, QW);
         const int nq64 = qlen <= QW ? qlen : -1;   // overflowed queue: the FP64 sum scans every atom
-        const int cpad = (K + 1) & ~1;             // padding candidate (far, no molecule)
         if (PREC == MC_PREC_FP64) {
             const int dec = exact(G.thr64[jr], nq64);
             if (dec < 0) status = MC_ST_BOND_BREAK;
@@ -1046,16 +889,13 @@ __device__ Res evaluate(const CellCtx &cx, const Group &G, const WarpScr &S, Nea
             const float thr32 = G.thr32[jr];
             Acc32 part;
             if (mvt == MC_MOVE_ATOM) {
-                part = inter_atom(G, S, nq, lane, md, cx.raw, k, cpad, wi, t3o[0], ho[0], hn[0], qo[0], qn[0], cx.hf,
-                                  cx.h2f);
+                part = inter_atom(G, S, nq, lane, md, K, k, wi, t3o[0], qo[0], qn[0], cx.h2f);
             } else if (mvt == MC_MOVE_FLIP) {
-                part = inter_flip(G, S, nq, lane, md, cx.raw, ks[0], ks[1], cpad, wi, t3o[0], t3o[1], ho[0], ho[1],
-                                  qo[0], qo[1], cx.hf, cx.h2f);
+                part = inter_flip(G, S, nq, lane, md, K, ks[0], ks[1], wi, t3o[0], t3o[1], qo[0], qo[1], cx.h2f);
             } else {
                 const int tm[3] = {t3o[0], t3o[1], t3o[2]};
-                const HiLo a[3] = {ho[0], ho[1], ho[2]}, b[3] = {hn[0], hn[1], hn[2]};
                 const Q3 ro[3] = {qo[0], qo[1], qo[2]}, rn[3] = {qn[0], qn[1], qn[2]};
-                part = inter_mol(G, S, nq, lane, md, cx.raw, tm, a, b, ro, rn, cx.hf, cx.h2f);
+                part = inter_mol(G, S, nq, lane, md, K, tm, ro, rn, cx.h2f);
                 if (mvt == MC_MOVE_MOL_ROT && lane == 0) part = rot_intra32(md, ro, rn, tm, cx.hf, part);
             }
             if (qlen > QW) part.guard = 1;
@@ -1100,7 +940,6 @@ __device__ Res evaluate(const CellCtx &cx, const Group &G, const WarpScr &S, Nea
         R.qn[s][0] = qn[s].x;
         R.qn[s][1] = qn[s].y;
         R.qn[s][2] = qn[s].z;
-        R.hn[s] = hn[s];
     }
     if (W > 1 && lane == 0) {
         // positions the move reads or writes, for the conflict test of the commit
@@ -1109,9 +948,11 @@ __device__ Res evaluate(const CellCtx &cx, const Group &G, const WarpScr &S, Nea
 #pragma unroll
             for (int s = 0; s < 3; ++s) {
                 if (s < nmv) {
-                    N->px[na] = ho[s].x; N->py[na] = ho[s].y; N->pz[na] = ho[s].z; ++na;
+                    const PosH o = local_of(cx, qo[s]);
+                    N->px[na] = o.x; N->py[na] = o.y; N->pz[na] = o.z; ++na;
                     if (mvt != MC_MOVE_FLIP) {
-                        N->px[na] = hn[s].x; N->py[na] = hn[s].y; N->pz[na] = hn[s].z; ++na;
+                        const PosH m = local_of(cx, qn[s]);
+                        N->px[na] = m.x; N->py[na] = m.y; N->pz[na] = m.z; ++na;
                     }
                 }
             }
@@ -1177,7 +1018,6 @@ __device__ __forceinline__ void commit(const Group &G, const Res &R, int at, int
                 int4 rs = G.rec[R.ks[s]];
                 rs.w = (rs.w & ~3) | R.t3n[s];
                 G.rec[R.ks[s]] = rs;
-                G.sw[R.ks[s]] = rs.w;
             }
         } else {
 #pragma unroll
@@ -1189,10 +1029,6 @@ __device__ __forceinline__ void commit(const Group &G, const Res &R, int at, int
                     rs.y = (int)R.qn[s][1];
                     rs.z = (int)R.qn[s][2];
                     G.rec[ks] = rs;
-                    G.sx[ks] = R.hn[s].x;
-                    G.sy[ks] = R.hn[s].y;
-                    G.sz[ks] = R.hn[s].z;
-                    G.sl[ks] = R.hn[s].lo;
                 }
             }
         }
@@ -1329,7 +1165,6 @@ __device__ void run_cell(const DevState &d, int buf, int colour, const LogArgs &
     c.n = n;
     c.cellL = cellL;
     c.nc = nc;
-    c.raw = raw;
     c.shift[0] = ct.shift[0];
     c.shift[1] = ct.shift[1];
     c.shift[2] = ct.shift[2];
@@ -1347,15 +1182,9 @@ __device__ void run_cell(const DevState &d, int buf, int colour, const LogArgs &
     float rc2max = 0.f;
     for (int kk = 0; kk < 9; ++kk) rc2max = fmaxf(rc2max, md.rc2f[kk]);
     c.pre_r2 = rc2max * 1.01f;
-    c.r2q = raw ? c.pre_r2 : c.pre_r2 / c.h2f;
+    c.r2q = c.pre_r2 / c.h2f;
     const float rconf = rc2max * 1.0201f / c.h2f;   // (1.01 rc)^2, fixed-point units
     c.rv.smem = G.rec;
-    c.rv.full = true;
-    c.rv.n = n;
-    c.rv.gsrc = d.rec[buf];
-    c.rv.cstart = G.cstart;
-    c.rv.coff = G.coff;
-    c.rv.ns = ns;
 
     // ---- stage: the random words of the first 32 attempts load while the
     // bulk copies land; then the records are split into the screening arrays ----
@@ -1384,16 +1213,7 @@ __device__ void run_cell(const DevState &d, int buf, int colour, const LogArgs &
             }
         }
         if (!ok) G.misc[MS_FAIL] = 1;
-        for (int idx = gt; ok && idx < K; idx += T) {
-            const int4 rc = G.rec[idx];
-            if (idx < n) G.orig[idx] = rc;
-            G.sw[idx] = rc.w;
-            const HiLo hl = hilo_of(c, Q3{(uint32_t)rc.x, (uint32_t)rc.y, (uint32_t)rc.z});
-            G.sx[idx] = hl.x;
-            G.sy[idx] = hl.y;
-            G.sz[idx] = hl.z;
-            G.sl[idx] = hl.lo;
-        }
+        for (int idx = gt; ok && idx < n; idx += T) G.orig[idx] = G.rec[idx];   // the own cell as staged
         if (has_rnd) {
             uint4 *wv = (uint4 *)(G.rnd + 8 * a);
             wv[0] = rb0;
@@ -1401,17 +1221,9 @@ __device__ void run_cell(const DevState &d, int buf, int colour, const LogArgs &
             if (PREC == MC_PREC_FP64) G.thr64[a] = th64;
             else G.thr32[a] = th32;
         }
-        if (gt < PADS) {
-            // padding candidates: far away, no molecule (the screens and the
-            // interaction passes read them instead of branching)
-            const int i = K + gt;
-            G.sx[i] = FAR;
-            G.sy[i] = FAR;
-            G.sz[i] = FAR;
-            G.sl[i] = 0;
-            G.sw[i] = PAD_W;
-            G.rec[i] = make_int4(0, 0, 0, PAD_W);
-        }
+        // padding records: no molecule, never within reach (the screens and the
+        // interaction passes read them instead of branching)
+        if (gt < PADS) G.rec[K + gt] = make_int4(0, 0, 0, PAD_W);
     }
     gsync<W>(gid);
     if (G.misc[MS_FAIL]) {
