@@ -59,7 +59,7 @@ constexpr int BLOCK = 128;          // threads per block (all W)
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int PADS = kPadSlots;     // padding candidates staged after the K atoms
 constexpr int PAD_W = kPadWord;     // their record word: type 0, a molecule no atom has
-constexpr int SCREEN_U = 8;         // 32-candidate steps per screening block
+constexpr int SCREEN_U = 4;         // 64-candidate steps per screening block
 
 // ---------------------------------------------------------------------------
 // packed FP32 pairs (f32x2, sm_100 and later)
@@ -478,9 +478,9 @@ __device__ __noinline__ void rotate_molecule(const uint32_t (*q)[3], uint32_t (*
 // ---------------------------------------------------------------------------
 // Candidate screens: queue every partner within the screening radius of an
 // old or new position of a moved atom (and, for single-atom moves and flips,
-// every atom of the molecule).  A lane takes one candidate per 32-candidate
-// step; the loads and arithmetic of SCREEN_U steps are issued before any queue
-// store, and the queue is filled in ballot order afterwards.  Lanes past the
+// every atom of the molecule).  The loads and arithmetic of SCREEN_U steps are
+// issued before any queue store, and the queue is filled in ballot order
+// afterwards.  Lanes past the
 // K staged atoms read the first padding record (no molecule, never within
 // reach), so no lane branches; entries past QW are counted but not stored.
 // ---------------------------------------------------------------------------
@@ -495,29 +495,50 @@ __device__ __forceinline__ void queue_step(const WarpScr &S, int lane, int &qlen
     qlen += __popc(b);
 }
 
+// append the hits of one 64-candidate step (candidate c = base + 2 lane for
+// bit b0, c + 1 for b1) in ballot order, the same way
+__device__ __forceinline__ void queue_step2(const WarpScr &S, int lane, int &qlen, unsigned b0, unsigned b1, int c)
+{
+    const unsigned lt = (1u << lane) - 1u;
+    const int e0 = ((b0 >> lane) & 1u) ? min(qlen + __popc(b0 & lt), QW) : QW;
+    const int e1 = ((b1 >> lane) & 1u) ? min(qlen + __popc(b0) + __popc(b1 & lt), QW) : QW;
+    S.qc[e0] = c;
+    S.qc[e1] = c + 1;
+    qlen += __popc(b0) + __popc(b1);
+}
+
 // Atom translation from qo to qo + e: the old distance from the exact int32
-// difference, the new one as r'^2 = r^2 - 2 d.e + |e|^2 (fixed-point units).
+// differences, the new one as r'^2 = r^2 - 2 d.e + |e|^2 (fixed-point units);
+// a lane takes two consecutive candidates per step, in packed FP32 pairs.
 __device__ __forceinline__ int screen_atom(const Group &G, const WarpScr &S, int K, int lane, const Q3 &qo,
                                            const Q3 &qn, int wi, float r2q)
 {
     const float ex = dq(qn.x, qo.x), ey = dq(qn.y, qo.y), ez = dq(qn.z, qo.z);
-    const float mx = -2.f * ex, my = -2.f * ey, mz = -2.f * ez;
+    const f2_t mx = pk(-2.f * ex, -2.f * ex), my = pk(-2.f * ey, -2.f * ey), mz = pk(-2.f * ez, -2.f * ez);
     const float ee = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+    const f2_t e2 = pk(ee, ee);
     int qlen = 0;
-    for (int base = 0; base < K; base += 32 * SCREEN_U) {
-        unsigned b[SCREEN_U];
+    for (int base = 0; base < K; base += 64 * SCREEN_U) {
+        unsigned b0[SCREEN_U], b1[SCREEN_U];
 #pragma unroll
         for (int u = 0; u < SCREEN_U; ++u) {
-            const int c = base + 32 * u + lane;
-            const int4 r = G.rec[c < K ? c : K];
-            const float dx = dq((uint32_t)r.x, qo.x), dy = dq((uint32_t)r.y, qo.y), dz = dq((uint32_t)r.z, qo.z);
-            const float r2o = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-            const float r2n = fmaf(dz, mz, fmaf(dy, my, fmaf(dx, mx, r2o + ee)));
-            const bool near = (fminf(r2o, r2n) < r2q) & (r.w != PAD_W);
-            b[u] = __ballot_sync(FULL, near | ((r.w ^ wi) < 16));
+            const int c = base + 64 * u + 2 * lane;
+            const int4 r0 = G.rec[c < K ? c : K], r1 = G.rec[c + 1 < K ? c + 1 : K];
+            const f2_t X = pk(dq((uint32_t)r0.x, qo.x), dq((uint32_t)r1.x, qo.x));
+            const f2_t Y = pk(dq((uint32_t)r0.y, qo.y), dq((uint32_t)r1.y, qo.y));
+            const f2_t Z = pk(dq((uint32_t)r0.z, qo.z), dq((uint32_t)r1.z, qo.z));
+            const f2_t r2o = fma2(Z, Z, fma2(Y, Y, mul2(X, X)));
+            const f2_t r2n = fma2(Z, mz, fma2(Y, my, fma2(X, mx, add2(r2o, e2))));
+            float a0, a1, n0, n1;
+            upk(r2o, a0, a1);
+            upk(r2n, n0, n1);
+            const bool p0 = ((fminf(a0, n0) < r2q) & (r0.w != PAD_W)) | ((r0.w ^ wi) < 16);
+            const bool p1 = ((fminf(a1, n1) < r2q) & (r1.w != PAD_W)) | ((r1.w ^ wi) < 16);
+            b0[u] = __ballot_sync(FULL, p0);
+            b1[u] = __ballot_sync(FULL, p1);
         }
 #pragma unroll
-        for (int u = 0; u < SCREEN_U; ++u) queue_step(S, lane, qlen, b[u], base + 32 * u + lane);
+        for (int u = 0; u < SCREEN_U; ++u) queue_step2(S, lane, qlen, b0[u], b1[u], base + 64 * u + 2 * lane);
     }
     return qlen;
 }
@@ -527,17 +548,30 @@ __device__ __forceinline__ int screen_flip(const Group &G, const WarpScr &S, int
                                            const Q3 &qq, int wi, float r2q)
 {
     int qlen = 0;
-    for (int base = 0; base < K; base += 32 * SCREEN_U) {
-        unsigned b[SCREEN_U];
+    for (int base = 0; base < K; base += 64 * SCREEN_U) {
+        unsigned b0[SCREEN_U], b1[SCREEN_U];
 #pragma unroll
         for (int u = 0; u < SCREEN_U; ++u) {
-            const int c = base + 32 * u + lane;
-            const int4 r = G.rec[c < K ? c : K];
-            const bool near = (fminf(r2_q(r, qp), r2_q(r, qq)) < r2q) & (r.w != PAD_W);
-            b[u] = __ballot_sync(FULL, near | ((r.w ^ wi) < 16));
+            const int c = base + 64 * u + 2 * lane;
+            const int4 r0 = G.rec[c < K ? c : K], r1 = G.rec[c + 1 < K ? c + 1 : K];
+            f2_t X = pk(dq((uint32_t)r0.x, qp.x), dq((uint32_t)r1.x, qp.x));
+            f2_t Y = pk(dq((uint32_t)r0.y, qp.y), dq((uint32_t)r1.y, qp.y));
+            f2_t Z = pk(dq((uint32_t)r0.z, qp.z), dq((uint32_t)r1.z, qp.z));
+            const f2_t rp = fma2(Z, Z, fma2(Y, Y, mul2(X, X)));
+            X = pk(dq((uint32_t)r0.x, qq.x), dq((uint32_t)r1.x, qq.x));
+            Y = pk(dq((uint32_t)r0.y, qq.y), dq((uint32_t)r1.y, qq.y));
+            Z = pk(dq((uint32_t)r0.z, qq.z), dq((uint32_t)r1.z, qq.z));
+            const f2_t rq = fma2(Z, Z, fma2(Y, Y, mul2(X, X)));
+            float a0, a1, n0, n1;
+            upk(rp, a0, a1);
+            upk(rq, n0, n1);
+            const bool p0 = ((fminf(a0, n0) < r2q) & (r0.w != PAD_W)) | ((r0.w ^ wi) < 16);
+            const bool p1 = ((fminf(a1, n1) < r2q) & (r1.w != PAD_W)) | ((r1.w ^ wi) < 16);
+            b0[u] = __ballot_sync(FULL, p0);
+            b1[u] = __ballot_sync(FULL, p1);
         }
 #pragma unroll
-        for (int u = 0; u < SCREEN_U; ++u) queue_step(S, lane, qlen, b[u], base + 32 * u + lane);
+        for (int u = 0; u < SCREEN_U; ++u) queue_step2(S, lane, qlen, b0[u], b1[u], base + 64 * u + 2 * lane);
     }
     return qlen;
 }
