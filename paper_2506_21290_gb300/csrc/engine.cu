@@ -531,6 +531,7 @@ int create_impl(mc_handle **out, int n_rep, const double *L, const int32_t *n_mo
         (rc = h->alloc(&h->d_c2, M_tot)) || (rc = h->alloc(&h->d_q, 6 * 256)) ||
         (rc = h->alloc(&h->d_obs_out, 3 * (size_t)n_rep)) ||
         (rc = h->alloc(&h->ds.att_rnd, 2 * (size_t)h->n_sites)) || (rc = h->alloc(&h->d_bar, 2)) ||
+        (rc = h->alloc(&h->ds.cell_done, h->n_cells)) ||
         (rc = h->alloc(&h->d_scan_tot, kMaxPersistentBlocks)) ||
         (rc = h->precision == MC_PREC_FP64 ? h->alloc(&h->ds.att_thr64, h->n_sites)
                                            : h->alloc(&h->ds.att_thr32, h->n_sites))) {
@@ -641,6 +642,7 @@ static int sweep_impl(mc_handle *h, int n_sweeps, const double *T, const mc_move
         // cell counts on entry and leaves them zero)
         CUDA_TRY(cudaMemsetAsync(h->ds.cell_count, 0, sizeof(int) * h->n_cells, h->stream));
         CUDA_TRY(cudaMemsetAsync(h->d_bar, 0, sizeof(unsigned int) * 2, h->stream));
+        CUDA_TRY(cudaMemsetAsync(h->ds.cell_done, 0, sizeof(unsigned int) * h->n_cells, h->stream));
         const int e = launch_persistent(h->ds, h->cur, n_sweeps, h->wpb, h->pgrid, h->d_bar, h->d_scan_tot, h->stream);
         if (e != 0) return fail(MC_ERR_CUDA, std::string("persistent sweep launch: ") + cudaGetErrorString((cudaError_t)e));
         h->cur ^= (n_sweeps & 1);

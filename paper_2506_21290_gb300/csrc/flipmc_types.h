@@ -109,6 +109,7 @@ struct DevState {
     unsigned long long *stats;   // STAT_N per replica
     double *e_run;       // per replica
     int *err;
+    unsigned int *cell_done;     // per cell: colour phases it completed in the current persistent launch
 };
 
 }  // namespace flipmc

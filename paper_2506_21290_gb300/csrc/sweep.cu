@@ -1105,11 +1105,41 @@ __device__ __forceinline__ void init_group(unsigned char *gsmem, const DevState 
     }
 }
 
+// Ordering of the colour phases inside one persistent launch, cell by cell:
+// a cell may start its phase of sweep s once every neighbour cell of a smaller
+// colour has finished its phase of sweep s (the neighbours' writes are then
+// visible, and none of them still reads this cell's atoms; neighbours of a
+// larger colour wait for this cell in turn).  done[c] counts the phases cell c
+// completed in the launch; dep = s + 1 (0: ordered by kernel boundaries).
+__device__ __forceinline__ void wait_done(const unsigned int *done, unsigned dep, int *err)
+{
+    unsigned spins = 0;
+    for (;;) {
+        unsigned v;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(done) : "memory");
+        if (v >= dep) return;
+        ++spins;
+        // bounded; and once any wait of the launch has given up, the others stop too
+        if ((spins & 4095u) == 0 && (*(volatile int *)err & ERR_TIMEOUT)) return;
+        if (spins > (1u << 21)) {
+            atomicOr(err, ERR_TIMEOUT);
+            return;
+        }
+    }
+}
+
+// The group's writes to the cell are complete (the caller synchronised the
+// group): publish them and count the phase.  One thread.
+__device__ __forceinline__ void signal_done(unsigned int *done)
+{
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(done) : "memory");
+}
+
 // All n attempts of active cell g of the colour, by the 32 W threads of one
 // group (group index gid within the block, its shared memory at gsmem).
 template <int PREC, int W>
 __device__ void run_cell(const DevState &d, int buf, int colour, const LogArgs &lg, int g, const ModelDev &md,
-                         const MixDev &mx, unsigned char *gsmem, int gid)
+                         const MixDev &mx, unsigned char *gsmem, int gid, unsigned dep)
 {
     constexpr int T = 32 * W;          // threads per cell
     const int gt = threadIdx.x % T;
@@ -1148,6 +1178,8 @@ __device__ void run_cell(const DevState &d, int buf, int colour, const LogArgs &
             }
             const int nx = (cx + ox + nc) % nc, ny = (cy + oy + nc) % nc, nz = (cz + oz + nc) % nc;
             const int c = ri.cell_off + (nz * nc + ny) * nc + nx;
+            const int ncol = (nx & 1) | ((ny & 1) << 1) | ((nz & 1) << 2);
+            if (dep != 0 && ncol < colour) wait_done(d.cell_done + c, dep, d.err);
             cst = d.cell_start[c];
             cnt = d.cell_start[c + 1] - cst;
         }
@@ -1188,6 +1220,7 @@ __device__ void run_cell(const DevState &d, int buf, int colour, const LogArgs &
         if (gt == 0) {
             atomicOr(d.err, ERR_STENCIL);
             d.cell_dE[cellG] = 0.0;
+            if (dep != 0) signal_done(d.cell_done + cellG);
         }
         return;
     }
@@ -1266,6 +1299,7 @@ __device__ void run_cell(const DevState &d, int buf, int colour, const LogArgs &
         if (gt == 0) atomicOr(d.err, ERR_TIMEOUT);
         for (unsigned t2 = 0; t2 < (1u << 22) && !mbar_done(G.mbar, parity); ++t2) {
         }
+        if (gt == 0 && dep != 0) signal_done(d.cell_done + cellG);
         return;
     }
     if (gt == 0) G.misc[MS_PHASE] = (int)(parity ^ 1u);   // every thread has read the parity
@@ -1374,6 +1408,12 @@ __device__ void run_cell(const DevState &d, int buf, int colour, const LogArgs &
         if (t.pairs) atomicAdd(st + STAT_PAIRS, t.pairs);
         if (t.rechecks) atomicAdd(st + STAT_RECHECK, (unsigned long long)t.rechecks);
     }
+    if (dep != 0) {
+        // every thread's write-back precedes the signal
+        if constexpr (W == 1) __syncwarp();
+        else gsync<W>(gid);
+        if (gt == 0) signal_done(d.cell_done + cellG);
+    }
 }
 
 // One colour phase, one launch: group g of the grid owns active cell g.
@@ -1392,7 +1432,7 @@ __global__ void __launch_bounds__(BLOCK, W == 1 ? 3 : 1) phase_kernel(DevState d
     __syncthreads();
     const int g = blockIdx.x * CPB + gid;
     if (g >= d.n_act) return;          // whole group leaves together
-    run_cell<PREC, W>(d, buf, colour, lg, g, md, mx, gsmem, gid);
+    run_cell<PREC, W>(d, buf, colour, lg, g, md, mx, gsmem, gid, 0u);
 }
 
 // Per replica (one block of BLOCK threads): add the sweep's accepted Delta E,
@@ -1455,7 +1495,12 @@ __device__ bool grid_sync(const GridBar &gb, unsigned int &target, int *err)
             unsigned int v;
             asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(gb.count) : "memory");
             if ((int)(v - target) >= 0) break;
-            if (++spins > (1ull << 23)) {
+            ++spins;
+            if ((spins & 4095u) == 0 && (*(volatile int *)err & ERR_TIMEOUT)) {
+                ok = 0;
+                break;
+            }
+            if (spins > (1ull << 23)) {
                 atomicOr(err, ERR_TIMEOUT);
                 ok = 0;
                 break;
@@ -1553,12 +1598,12 @@ __global__ void __launch_bounds__(BLOCK, W == 1 ? 3 : 1) sweep_persistent(DevSta
         for (int c = blockIdx.x * (BLOCK / 32) + warp; c < nC; c += gridDim.x * (BLOCK / 32))
             cl_order_cell(d, buf ^ 1, c, lane);
         if (!grid_sync(gb, bar_target, d.err)) return;
-        // ---- the 8 colours ----
-        for (int colour = 0; colour < 8; ++colour) {
+        // ---- the 8 colours, ordered cell by cell (no grid-wide barrier between
+        // colours: each cell waits for its neighbours of smaller colours) ----
+        for (int colour = 0; colour < 8; ++colour)
             for (int g = blockIdx.x * CPB + gid; g < d.n_act; g += gridDim.x * CPB)
-                run_cell<PREC, W>(d, buf ^ 1, colour, none, g, md, mx, gsmem, gid);
-            if (!grid_sync(gb, bar_target, d.err)) return;
-        }
+                run_cell<PREC, W>(d, buf ^ 1, colour, none, g, md, mx, gsmem, gid, (unsigned)s + 1u);
+        if (!grid_sync(gb, bar_target, d.err)) return;
         // ---- finalise the sweep; clear the counts for the next one ----
         for (int r = blockIdx.x; r < d.n_rep; r += gridDim.x) finalize_replica(d, r, red);
         for (int c = tid; c < nC; c += nthr) d.cell_count[c] = 0;
