@@ -1165,9 +1165,14 @@ __device__ void run_cell(const DevState &d, int buf, int colour, const LogArgs &
     const bool raw = nc == 2;
     const int ns = raw ? 8 : 27;
 
-    // ---- neighbourhood: own cell first ----
+    // ---- neighbourhood: own cell first.  The extents of the cells and the
+    // random words of the first 32 attempts are loaded before waiting for the
+    // neighbours (both are fixed for the sweep); the records only after ----
+    uint4 rb0 = make_uint4(0, 0, 0, 0), rb1 = rb0;   // warp 0: attempt `lane`'s draws
+    double th64 = 0.0;
+    float th32 = 0.f;
     if (wig == 0) {
-        int cnt = 0, cst = 0;
+        int cnt = 0, cst = 0, wait_c = -1;
         if (lane < ns) {
             int ox, oy, oz;
             if (raw) {
@@ -1179,10 +1184,21 @@ __device__ void run_cell(const DevState &d, int buf, int colour, const LogArgs &
             const int nx = (cx + ox + nc) % nc, ny = (cy + oy + nc) % nc, nz = (cz + oz + nc) % nc;
             const int c = ri.cell_off + (nz * nc + ny) * nc + nx;
             const int ncol = (nx & 1) | ((ny & 1) << 1) | ((nz & 1) << 2);
-            if (dep != 0 && ncol < colour) wait_done(d.cell_done + c, dep, d.err);
+            if (dep != 0 && ncol < colour) wait_c = c;
             cst = d.cell_start[c];
             cnt = d.cell_start[c + 1] - cst;
         }
+        {
+            const int n0 = __shfl_sync(FULL, cnt, 0), s0 = __shfl_sync(FULL, cst, 0);
+            if (lane < n0) {
+                const size_t slot = (size_t)s0 + (size_t)lane;
+                rb0 = d.att_rnd[2 * slot];
+                rb1 = d.att_rnd[2 * slot + 1];
+                if (PREC == MC_PREC_FP64) th64 = d.att_thr64[slot];
+                else th32 = d.att_thr32[slot];
+            }
+        }
+        if (wait_c >= 0) wait_done(d.cell_done + wait_c, dep, d.err);
         int incl = cnt;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -1253,21 +1269,11 @@ __device__ void run_cell(const DevState &d, int buf, int colour, const LogArgs &
     const float rconf = rc2max * 1.0201f / c.h2f;   // (1.01 rc)^2, fixed-point units
     c.rv.smem = G.rec;
 
-    // ---- stage: the random words of the first 32 attempts load while the
-    // bulk copies land; then the records are split into the screening arrays ----
+    // ---- stage: wait for the bulk copies, keep a copy of the own cell, store
+    // the first 32 attempts' draws ----
     {
         const int a = gt;
-        const bool has_rnd = gt < 32 && gt < n;
-        uint4 rb0 = make_uint4(0, 0, 0, 0), rb1 = rb0;
-        double th64 = 0.0;
-        float th32 = 0.f;
-        if (has_rnd) {
-            const size_t slot = (size_t)own_start + (size_t)a;
-            rb0 = d.att_rnd[2 * slot];
-            rb1 = d.att_rnd[2 * slot + 1];
-            if (PREC == MC_PREC_FP64) th64 = d.att_thr64[slot];
-            else th32 = d.att_thr32[slot];
-        }
+        const bool has_rnd = gt < 32 && gt < n;   // warp 0, which loaded them
         // bounded wait for the copies (every thread: the barrier's completion
         // makes the copied bytes visible to the waiting thread); a thread that
         // gives up marks the cell, and the group leaves it together below
