@@ -1383,10 +1383,16 @@ __device__ void run_cell(const DevState &d, int buf, int colour, const LogArgs &
         }
         dst[kk] = nw;
     }
-    // ---- counts: the warps' tallies in warp order ----
+    // ---- publish the cell to the neighbours waiting for it (before the
+    // counts, which nobody waits for); then the warps' tallies in warp order ----
     if constexpr (W > 1) {
         if (lane == 0) G.tally[wig] = t;
-        gsync<W>(gid);
+        gsync<W>(gid);   // every write-back and tally is done
+    } else {
+        __syncwarp();
+    }
+    if (gt == 0 && dep != 0) signal_done(d.cell_done + cellG);
+    if constexpr (W > 1) {
         if (gt == 0)
             for (int j = 1; j < W; ++j) {
                 const Tally &u = G.tally[j];
@@ -1413,12 +1419,6 @@ __device__ void run_cell(const DevState &d, int buf, int colour, const LogArgs &
         if (t.rej_bond) atomicAdd(st + STAT_REJ_BOND, (unsigned long long)t.rej_bond);
         if (t.pairs) atomicAdd(st + STAT_PAIRS, t.pairs);
         if (t.rechecks) atomicAdd(st + STAT_RECHECK, (unsigned long long)t.rechecks);
-    }
-    if (dep != 0) {
-        // every thread's write-back precedes the signal
-        if constexpr (W == 1) __syncwarp();
-        else gsync<W>(gid);
-        if (gt == 0) signal_done(d.cell_done + cellG);
     }
 }
 
