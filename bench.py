@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--precision", default="", choices=["", "fp32", "fp64"])
     ap.add_argument("--launch-mode", type=int, default=0, choices=[0, 1, 2],
                     help="0 auto, 1 a CUDA graph per sweep, 2 one persistent launch per step")
-    ap.add_argument("--warps-per-cell", type=int, default=0, choices=[0, 1, 2, 4])
+    ap.add_argument("--warps-per-cell", type=int, default=0, choices=[0, 1, 2, 4, 8])
     ap.add_argument("--recheck-gap", type=float, default=0.0, help="FP32 decision margin (0: library default)")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -280,8 +280,8 @@ def run_native(args):
     if args.autotune > 0 and args.warps_per_cell == 0 and args.launch_mode == 0:
         # pick the cell schedule on a copy of the state (the chain is unchanged)
         res = h.autotune(args.autotune, wl["T"], mix, wl["seeds"])
-        tuned = {"ms_per_sweep": {"persistent": [float(x) for x in res[:3]], "graphs": [float(x) for x in res[3:]]},
-                 "warps_per_cell": [1, 2, 4], "sweeps_per_trial": args.autotune}
+        tuned = {"ms_per_sweep": {"persistent": [float(x) for x in res[:4]], "graphs": [float(x) for x in res[4:]]},
+                 "warps_per_cell": [1, 2, 4, 8], "sweeps_per_trial": args.autotune}
     # a dedicated stream: the library enqueues on it, the events are recorded on it
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)

@@ -107,7 +107,7 @@ typedef struct {
  * default every decision taken in FP32 is the one FP64 takes; smaller values
  * trade that guarantee for fewer FP64 rechecks.  device: CUDA device
  * ordinal.  stencil_cap: atoms staged per cell neighbourhood (0 = automatic).
- * warps_per_cell: 1, 2 or 4 warps per cell, each evaluating one of the cell's
+ * warps_per_cell: 1, 2, 4 or 8 warps per cell, each evaluating one of the cell's
  * consecutive attempts, committed in order (0 = chosen from the number of
  * cells); results do not depend on it.  launch_mode: 0 = one persistent
  * cooperative launch per mc_sweep call when the device supports it, else a
@@ -300,7 +300,7 @@ int mc_observables(mc_handle *h, const double *qvec_atom, int n_qa, const double
  * the statistics are restored afterwards: the chain continues exactly as if
  * the call had not been made (the schedule never changes the chain).  The
  * arguments T, mix and seeds are those of mc_sweep_batch.  results (nullable,
- * host, 6 doubles): ms per sweep for W = 1, 2, 4 persistent, then W = 1, 2, 4
+ * host, 8 doubles): ms per sweep for W = 1, 2, 4, 8 persistent, then W = 1, 2, 4, 8
  * graphs; a schedule that cannot run reads -1.  Not part of the paper's method:
  * an engineering choice of the library.  Errors: INVALID_ARG, CUDA. */
 int mc_autotune(mc_handle *h, int n_sweeps, const double *T, const mc_move_mix *mix, const uint64_t *seeds,

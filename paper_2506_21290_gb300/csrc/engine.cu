@@ -479,9 +479,10 @@ int create_impl(mc_handle **out, int n_rep, const double *L, const int32_t *n_mo
     h->stencil_cap = cap;
     // warps per cell: spread small grids over more warps so that every SM has
     // work; large grids keep one warp per cell (enough cells to fill the GPU)
-    if (o.warps_per_cell != 0 && o.warps_per_cell != 1 && o.warps_per_cell != 2 && o.warps_per_cell != 4) {
+    if (o.warps_per_cell != 0 && o.warps_per_cell != 1 && o.warps_per_cell != 2 && o.warps_per_cell != 4 &&
+        o.warps_per_cell != 8) {
         delete h;
-        return fail(MC_ERR_INVALID_ARG, "warps_per_cell must be 0, 1, 2 or 4");
+        return fail(MC_ERR_INVALID_ARG, "warps_per_cell must be 0, 1, 2, 4 or 8");
     }
     if (o.warps_per_cell > 0) h->wpb = o.warps_per_cell;
     else h->wpb = h->n_act >= 152 * 12 ? 1 : (h->n_act >= 152 * 3 ? 2 : 4);
@@ -782,12 +783,12 @@ int mc_autotune(mc_handle *h, int n_sweeps, const double *T, const mc_move_mix *
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    const int Ws[3] = {1, 2, 4};
+    const int Ws[4] = {1, 2, 4, 8};
     double best = 1e300;
     int bestW = W0;
     bool bestP = p0;
     for (int form = 0; form < 2; ++form) {
-        for (int k = 0; k < 3; ++k) {
+        for (int k = 0; k < 4; ++k) {
             double ms = -1.0;
             if (set_schedule(h, Ws[k], form == 0) == MC_OK) {
                 copy_all(false);
@@ -809,7 +810,7 @@ int mc_autotune(mc_handle *h, int n_sweeps, const double *T, const mc_move_mix *
                     }
                 }
             }
-            if (results) results[3 * form + k] = ms;
+            if (results) results[4 * form + k] = ms;
         }
     }
     copy_all(false);

@@ -55,7 +55,11 @@ namespace flipmc {
 
 constexpr int TERM_CAP = 128;       // nonzero FP64 terms of one move
 constexpr int QW = 64;              // interaction queue entries per warp
-constexpr int BLOCK = 128;          // threads per block (all W)
+constexpr int BLOCK = 128;          // threads per block for W <= 4 (and of the per-replica sums)
+
+// threads per block of the sweep kernels: BLOCK, or one group of W warps when W > 4
+template <int W>
+__host__ __device__ constexpr int block_threads() { return W > 4 ? 32 * W : BLOCK; }
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int PADS = kPadSlots;     // padding candidates staged after the K atoms
 constexpr int PAD_W = kPadWord;     // their record word: type 0, a molecule no atom has
@@ -228,7 +232,7 @@ struct Group {
     unsigned char *warp_base;   // W per-warp scratch blocks
 };
 
-enum { MS_K = 0, MS_N = 1, MS_START = 2, MS_PHASE = 3, MS_CLASH = 4, MS_FAIL = 8 };
+enum { MS_K = 0, MS_N = 1, MS_START = 2, MS_PHASE = 3, MS_CLASH = 4 /* [W <= 8] */, MS_FAIL = 16 };
 
 __host__ __device__ constexpr size_t al16(size_t x) { return (x + 15) & ~size_t(15); }
 
@@ -1425,9 +1429,10 @@ __device__ void run_cell(const DevState &d, int buf, int colour, const LogArgs &
 // One colour phase, one launch: group g of the grid owns active cell g.
 // W = 1 serves large grids (many cells per SM): registers for three resident blocks
 template <int PREC, int W>
-__global__ void __launch_bounds__(BLOCK, W == 1 ? 3 : 1) phase_kernel(DevState d, int buf, int colour, LogArgs lg)
+__global__ void __launch_bounds__(block_threads<W>(), W == 1 ? 3 : 1) phase_kernel(DevState d, int buf, int colour,
+                                                                                 LogArgs lg)
 {
-    constexpr int CPB = BLOCK / (32 * W);
+    constexpr int CPB = block_threads<W>() / (32 * W);
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ ModelDev md;
     __shared__ MixDev mx;
@@ -1441,16 +1446,19 @@ __global__ void __launch_bounds__(BLOCK, W == 1 ? 3 : 1) phase_kernel(DevState d
     run_cell<PREC, W>(d, buf, colour, lg, g, md, mx, gsmem, gid, 0u);
 }
 
-// Per replica (one block of BLOCK threads): add the sweep's accepted Delta E,
-// the cells summed in a fixed partition and reduction tree so the result is
-// reproducible; count the sweep; advance the sweep counter.
+// Per replica (one block of at least BLOCK threads): add the sweep's accepted
+// Delta E, the cells summed in a fixed partition over BLOCK lanes and a fixed
+// reduction tree, whatever the block size, so the result is reproducible and
+// the same for every schedule; count the sweep; advance the sweep counter.
 __device__ void finalize_replica(const DevState &d, int r, double *red)
 {
     const RepInfo ri = d.rep[r];
     const int ncell = ri.nc * ri.nc * ri.nc;
-    double s = 0.0;
-    for (int c = threadIdx.x; c < ncell; c += BLOCK) s = __dadd_rn(s, d.cell_dE[ri.cell_off + c]);
-    red[threadIdx.x] = s;
+    if (threadIdx.x < BLOCK) {
+        double s = 0.0;
+        for (int c = threadIdx.x; c < ncell; c += BLOCK) s = __dadd_rn(s, d.cell_dE[ri.cell_off + c]);
+        red[threadIdx.x] = s;
+    }
     __syncthreads();
     for (int w = BLOCK / 2; w > 0; w >>= 1) {
         if (threadIdx.x < w) red[threadIdx.x] = __dadd_rn(red[threadIdx.x], red[threadIdx.x + w]);
@@ -1517,7 +1525,8 @@ __device__ bool grid_sync(const GridBar &gb, unsigned int &target, int *err)
     return ok != 0;
 }
 
-// exclusive prefix sum over a block of BLOCK threads (one value per thread)
+// exclusive prefix sum over a block of NT threads (one value per thread)
+template <int NT>
 __device__ __forceinline__ int block_excl_scan(int v, int *tmp, int &total)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1531,7 +1540,7 @@ __device__ __forceinline__ int block_excl_scan(int v, int *tmp, int &total)
     __syncthreads();
     int before = 0;
     total = 0;
-    for (int w = 0; w < BLOCK / 32; ++w) {
+    for (int w = 0; w < NT / 32; ++w) {
         if (w < warp) before += tmp[w];
         total += tmp[w];
     }
@@ -1540,22 +1549,24 @@ __device__ __forceinline__ int block_excl_scan(int v, int *tmp, int &total)
 }
 
 template <int PREC, int W>
-__global__ void __launch_bounds__(BLOCK, W == 1 ? 3 : 1) sweep_persistent(DevState d, int buf0, int n_sweeps, GridBar gb)
+__global__ void __launch_bounds__(block_threads<W>(), W == 1 ? 3 : 1) sweep_persistent(DevState d, int buf0,
+                                                                                     int n_sweeps, GridBar gb)
 {
     constexpr int T = 32 * W;
-    constexpr int CPB = BLOCK / T;
+    constexpr int NT = block_threads<W>();
+    constexpr int CPB = NT / T;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ ModelDev md;
     __shared__ MixDev mx;
     __shared__ double red[BLOCK];
-    __shared__ int tmp[BLOCK / 32];
+    __shared__ int tmp[NT / 32];
     const int gid = threadIdx.x / T;
     unsigned char *gsmem = smem + (size_t)gid * group_bytes(d.stencil_cap, d.own_cap, W);
     init_group(gsmem, d, W);
     load_tables(d, md, mx);
     __syncthreads();
-    const int nthr = gridDim.x * BLOCK;
-    const int tid = blockIdx.x * BLOCK + threadIdx.x;
+    const int nthr = gridDim.x * NT;
+    const int tid = blockIdx.x * NT + threadIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const LogArgs none{nullptr, 0, 0};
     const int nC = d.n_cells;
@@ -1570,28 +1581,28 @@ __global__ void __launch_bounds__(BLOCK, W == 1 ? 3 : 1) sweep_persistent(DevSta
         // ---- exclusive scan: chunk totals, then each block scans its chunk ----
         {
             int sum = 0;
-            for (int c = lo + threadIdx.x; c < hi; c += BLOCK) sum += d.cell_count[c];
+            for (int c = lo + threadIdx.x; c < hi; c += NT) sum += d.cell_count[c];
             int total;
-            block_excl_scan(sum, tmp, total);
+            block_excl_scan<NT>(sum, tmp, total);
             if (threadIdx.x == 0) gb.scan_tot[blockIdx.x] = total;
         }
         if (!grid_sync(gb, bar_target, d.err)) return;
         {
             int off = 0, all = 0;
-            for (int b = threadIdx.x; b < (int)gridDim.x; b += BLOCK) {
+            for (int b = threadIdx.x; b < (int)gridDim.x; b += NT) {
                 const int v = gb.scan_tot[b];
                 all += v;
                 if (b < (int)blockIdx.x) off += v;
             }
             int t1, t2;
-            block_excl_scan(off, tmp, t1);
-            block_excl_scan(all, tmp, t2);
+            block_excl_scan<NT>(off, tmp, t1);
+            block_excl_scan<NT>(all, tmp, t2);
             int carry = t1;                       // sum of the totals of earlier blocks
-            for (int base = lo; base < hi; base += BLOCK) {
+            for (int base = lo; base < hi; base += NT) {
                 const int c = base + threadIdx.x;
                 const int v = c < hi ? d.cell_count[c] : 0;
                 int tile;
-                const int ex = block_excl_scan(v, tmp, tile);
+                const int ex = block_excl_scan<NT>(v, tmp, tile);
                 if (c < hi) d.cell_start[c] = carry + ex;
                 carry += tile;
             }
@@ -1601,7 +1612,7 @@ __global__ void __launch_bounds__(BLOCK, W == 1 ? 3 : 1) sweep_persistent(DevSta
         // ---- scatter, then order each cell and draw its attempts' random numbers ----
         for (int g = tid; g < d.n_sites; g += nthr) cl_scatter_item(d, buf, buf ^ 1, g);
         if (!grid_sync(gb, bar_target, d.err)) return;
-        for (int c = blockIdx.x * (BLOCK / 32) + warp; c < nC; c += gridDim.x * (BLOCK / 32))
+        for (int c = blockIdx.x * (NT / 32) + warp; c < nC; c += gridDim.x * (NT / 32))
             cl_order_cell(d, buf ^ 1, c, lane);
         if (!grid_sync(gb, bar_target, d.err)) return;
         // ---- the 8 colours, ordered cell by cell (no grid-wide barrier between
@@ -1620,7 +1631,8 @@ __global__ void __launch_bounds__(BLOCK, W == 1 ? 3 : 1) sweep_persistent(DevSta
 
 size_t phase_smem_bytes(int stencil_cap, int own_cap, int warps_per_cell)
 {
-    return group_bytes(stencil_cap, own_cap, warps_per_cell) * (size_t)(BLOCK / (32 * warps_per_cell));
+    const int nt = warps_per_cell > 4 ? 32 * warps_per_cell : BLOCK;
+    return group_bytes(stencil_cap, own_cap, warps_per_cell) * (size_t)(nt / (32 * warps_per_cell));
 }
 
 template <class K>
@@ -1642,15 +1654,19 @@ int phase_set_smem_limit(int bytes_needed)
     ok &= set_kernel_smem(phase_kernel<MC_PREC_FP64, 1>, bytes);
     ok &= set_kernel_smem(phase_kernel<MC_PREC_FP64, 2>, bytes);
     ok &= set_kernel_smem(phase_kernel<MC_PREC_FP64, 4>, bytes);
+    ok &= set_kernel_smem(phase_kernel<MC_PREC_FP64, 8>, bytes);
     ok &= set_kernel_smem(phase_kernel<MC_PREC_FP32, 1>, bytes);
     ok &= set_kernel_smem(phase_kernel<MC_PREC_FP32, 2>, bytes);
     ok &= set_kernel_smem(phase_kernel<MC_PREC_FP32, 4>, bytes);
+    ok &= set_kernel_smem(phase_kernel<MC_PREC_FP32, 8>, bytes);
     ok &= set_kernel_smem(sweep_persistent<MC_PREC_FP64, 1>, bytes);
     ok &= set_kernel_smem(sweep_persistent<MC_PREC_FP64, 2>, bytes);
     ok &= set_kernel_smem(sweep_persistent<MC_PREC_FP64, 4>, bytes);
+    ok &= set_kernel_smem(sweep_persistent<MC_PREC_FP64, 8>, bytes);
     ok &= set_kernel_smem(sweep_persistent<MC_PREC_FP32, 1>, bytes);
     ok &= set_kernel_smem(sweep_persistent<MC_PREC_FP32, 2>, bytes);
     ok &= set_kernel_smem(sweep_persistent<MC_PREC_FP32, 4>, bytes);
+    ok &= set_kernel_smem(sweep_persistent<MC_PREC_FP32, 8>, bytes);
     const int full = cudaSharedmemCarveoutMaxShared;
     cudaFuncSetAttribute(finalize_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, full);
     cudaFuncSetAttribute(cl_count_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, full);
@@ -1663,11 +1679,13 @@ int phase_set_smem_limit(int bytes_needed)
 template <int PREC>
 static void launch_prec(const DevState &d, int buf, int W, const LogArgs &lg, cudaStream_t st)
 {
-    const int cpb = BLOCK / (32 * W);
+    const int nt = W > 4 ? 32 * W : BLOCK;
+    const int cpb = nt / (32 * W);
     const int blocks = (d.n_act + cpb - 1) / cpb;
     const size_t sm = phase_smem_bytes(d.stencil_cap, d.own_cap, W);
     for (int colour = 0; colour < 8; ++colour) {
-        if (W == 4) phase_kernel<PREC, 4><<<blocks, BLOCK, sm, st>>>(d, buf, colour, lg);
+        if (W == 8) phase_kernel<PREC, 8><<<blocks, 256, sm, st>>>(d, buf, colour, lg);
+        else if (W == 4) phase_kernel<PREC, 4><<<blocks, BLOCK, sm, st>>>(d, buf, colour, lg);
         else if (W == 2) phase_kernel<PREC, 2><<<blocks, BLOCK, sm, st>>>(d, buf, colour, lg);
         else phase_kernel<PREC, 1><<<blocks, BLOCK, sm, st>>>(d, buf, colour, lg);
     }
@@ -1698,8 +1716,15 @@ static void *persistent_fn()
 
 static void *persistent_kernel(int prec, int W)
 {
-    if (prec == MC_PREC_FP64) return W == 4 ? persistent_fn<MC_PREC_FP64, 4>() : W == 2 ? persistent_fn<MC_PREC_FP64, 2>() : persistent_fn<MC_PREC_FP64, 1>();
-    return W == 4 ? persistent_fn<MC_PREC_FP32, 4>() : W == 2 ? persistent_fn<MC_PREC_FP32, 2>() : persistent_fn<MC_PREC_FP32, 1>();
+    if (prec == MC_PREC_FP64)
+        return W == 8 ? persistent_fn<MC_PREC_FP64, 8>()
+               : W == 4 ? persistent_fn<MC_PREC_FP64, 4>()
+               : W == 2 ? persistent_fn<MC_PREC_FP64, 2>()
+                        : persistent_fn<MC_PREC_FP64, 1>();
+    return W == 8 ? persistent_fn<MC_PREC_FP32, 8>()
+           : W == 4 ? persistent_fn<MC_PREC_FP32, 4>()
+           : W == 2 ? persistent_fn<MC_PREC_FP32, 2>()
+                    : persistent_fn<MC_PREC_FP32, 1>();
 }
 
 int persistent_grid(const DevState &d, int warps_per_cell, int max_blocks)
@@ -1710,12 +1735,13 @@ int persistent_grid(const DevState &d, int warps_per_cell, int max_blocks)
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
     if (!coop) return 0;
     const size_t sm = phase_smem_bytes(d.stencil_cap, d.own_cap, warps_per_cell);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_kernel(d.precision, warps_per_cell), BLOCK,
-                                                      sm) != cudaSuccess)
+    const int nt = warps_per_cell > 4 ? 32 * warps_per_cell : BLOCK;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_kernel(d.precision, warps_per_cell), nt, sm) !=
+        cudaSuccess)
         return 0;
     // one block per group of active cells: blocks without a cell would only
     // add arrivals to every grid barrier
-    const int cpb = BLOCK / (32 * warps_per_cell);
+    const int cpb = nt / (32 * warps_per_cell);
     const int needed = std::max((d.n_act + cpb - 1) / cpb, 32);
     return std::max(0, std::min(std::min(per_sm * sms, needed), max_blocks));
 }
@@ -1727,8 +1753,9 @@ int launch_persistent(const DevState &d, int buf, int n_sweeps, int warps_per_ce
     GridBar gb{bar, scan_tot};
     DevState dd = d;
     void *args[] = {(void *)&dd, (void *)&buf, (void *)&n_sweeps, (void *)&gb};
+    const int nt = warps_per_cell > 4 ? 32 * warps_per_cell : BLOCK;
     const cudaError_t e = cudaLaunchCooperativeKernel(persistent_kernel(d.precision, warps_per_cell), dim3(grid),
-                                                      dim3(BLOCK), args, sm, st);
+                                                      dim3(nt), args, sm, st);
     return e == cudaSuccess ? 0 : (int)e;
 }
 

@@ -221,7 +221,7 @@ def mc_sweep_timed(h, n, Ts, mix, seeds):
 def mc_autotune(h, n, Ts, mix, seeds):
     Ts = np.ascontiguousarray(np.atleast_1d(Ts), dtype=np.float64)
     seeds = np.ascontiguousarray(np.atleast_1d(seeds), dtype=np.uint64)
-    res = np.zeros(6, dtype=np.float64)
+    res = np.zeros(8, dtype=np.float64)
     m = make_mix(mix)
     _check(load().mc_autotune(h, int(n), _ptr(Ts), C.byref(m), _ptr(seeds), _ptr(res)), "mc_autotune")
     return res
@@ -365,7 +365,7 @@ class Handle:
 
     def autotune(self, n, T, mix, seed):
         """Time every cell schedule on a copy of the state and keep the fastest;
-        returns ms per sweep [W=1, 2, 4 persistent, W=1, 2, 4 graphs] (-1: unavailable)."""
+        returns ms per sweep [W=1, 2, 4, 8 persistent, W=1, 2, 4, 8 graphs] (-1: unavailable)."""
         Ts = np.broadcast_to(np.asarray(T, dtype=np.float64), (self.n_rep,))
         seeds = np.broadcast_to(np.asarray(seed, dtype=np.uint64), (self.n_rep,))
         res = mc_autotune(self.h, n, Ts, mix, seeds)

@@ -99,7 +99,8 @@ def test_fp64_1000_molecules_bit_exact():
 @pytest.mark.parametrize("M,seed,T,mix,wpc", [(125, 4, 2.0, W.PAPER_MIX, 1), (125, 4, 2.0, W.PAPER_MIX, 2),
                                                (125, 4, 2.0, W.PAPER_MIX, 4), (216, 5, 0.75, W.RIGID_MIX, 1),
                                                (216, 5, 0.75, W.RIGID_MIX, 4), (64, 6, 3.0, W.PAPER_MIX, 2),
-                                               (343, 7, 1.1, W.PAPER_MIX, 0)])
+                                               (343, 7, 1.1, W.PAPER_MIX, 0), (343, 8, 1.1, W.PAPER_MIX, 8),
+                                               (216, 9, 0.75, W.RIGID_MIX, 8)])
 def test_fp32_same_decisions_and_dE_within_tolerance(M, seed, T, mix, wpc):
     L, xyz, t = _start(M, seed)
     h = F.Handle(L, xyz, t, POT, precision="fp32", warps_per_cell=wpc)
@@ -238,10 +239,9 @@ def test_autotune_leaves_the_chain_unchanged(precision, M):
     for h in (a, b):
         h.sweep(3, 1.4, W.PAPER_MIX, 23)
     res = a.autotune(3, 1.4, W.PAPER_MIX, 23)
-    assert res.shape == (6,) and (res > 0).any()
-    assert a.info["warps_per_cell"] in (1, 2, 4)
-    ms = {(1, True): res[0], (2, True): res[1], (4, True): res[2], (1, False): res[3], (2, False): res[4],
-          (4, False): res[5]}
+    assert res.shape == (8,) and (res > 0).any()
+    assert a.info["warps_per_cell"] in (1, 2, 4, 8)
+    ms = {(w, form == 0): res[4 * form + k] for form in (0, 1) for k, w in enumerate((1, 2, 4, 8))}
     chosen = ms[(a.info["warps_per_cell"], a.info["persistent_blocks"] > 0)]
     assert chosen == min(v for v in res if v > 0)
     for h in (a, b):
@@ -259,7 +259,7 @@ def test_autotune_leaves_the_chain_unchanged(precision, M):
 
 
 @pytest.mark.parametrize("precision,wpc,M", [("fp64", 1, 125), ("fp32", 1, 343), ("fp32", 2, 343), ("fp32", 4, 1000),
-                                             ("fp64", 4, 216)])
+                                             ("fp64", 4, 216), ("fp32", 8, 1000), ("fp64", 8, 125)])
 def test_persistent_launch_matches_graphs(precision, wpc, M):
     """One cooperative launch for all sweeps of a call gives the same chain,
     bit for bit, as one CUDA graph per sweep."""
