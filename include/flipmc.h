@@ -26,10 +26,12 @@
  * Precision.  MC_PREC_FP64 evaluates every Delta E in FP64 with one rounding per
  * operation, summed in a fixed order (moved atom ascending, then partner index
  * ascending); it reproduces the library's FP64 reference trajectory exactly.
- * MC_PREC_FP32 evaluates pair terms in FP32 and takes the Metropolis decision in
- * FP64: when |dE32 - threshold| is within recheck_gap times the sum of term
- * magnitudes, Delta E is recomputed in the FP64 order above.  Running and total
- * energies are FP64 in both modes.
+ * MC_PREC_FP32 evaluates pair terms in FP32 and decides in FP32 when
+ * |dE32 - threshold| exceeds recheck_gap times the sum of term magnitudes plus
+ * the threshold's own error bound (the FP32 decision then equals the FP64 one);
+ * otherwise it recomputes Delta E and the threshold in the FP64 order above.
+ * Total energies are FP64 in both modes; the running total is accumulated in
+ * FP64 (in FP32 mode from per-cell FP32 sums of the accepted FP32 Delta E).
  *
  * Conventions.  All functions return 0 (MC_OK) or a negative MC_ERR_* code;
  * mc_last_error() returns a message for the calling thread's last error.

@@ -474,7 +474,7 @@ int create_impl(mc_handle **out, int n_rep, const double *L, const int32_t *n_mo
     h->n_sites = (int)sites;
     h->n_cells = (int)cells;
     h->n_act = (int)act;
-    // staging capacity: the neighbourhood plus one padding slot, a multiple of 32
+    // staging capacity: the neighbourhood (mean + 6 sigma + 32) plus the padding records, a multiple of 32
     int cap = o.stencil_cap > 0 ? o.stencil_cap : ((int)std::ceil(max_stencil) + kPadSlots + 31) / 32 * 32;
     h->stencil_cap = cap;
     // warps per cell: spread small grids over more warps so that every SM has

@@ -1480,9 +1480,11 @@ __global__ void __launch_bounds__(BLOCK) finalize_kernel(DevState d)
 
 // ---------------------------------------------------------------------------
 // Persistent sweeps: one cooperative launch runs n_sweeps whole sweeps (cell
-// list, 8 colour phases, finalisation), the stages separated by a grid-wide
-// barrier.  Every wait of the barrier is bounded: after a few seconds it
-// records ERR_TIMEOUT and the kernel leaves, instead of waiting forever.
+// list, 8 colour phases, finalisation).  The cell-list stages and the
+// finalisation are separated by grid-wide barriers; the colour phases are
+// ordered cell by cell (run_cell).  Every wait is bounded: after a few
+// seconds it records ERR_TIMEOUT and the kernel leaves, instead of waiting
+// forever.
 // ---------------------------------------------------------------------------
 struct GridBar {
     unsigned int *count;  // arrivals since the launch began (zero at launch)
