@@ -11,7 +11,7 @@ namespace flipmc {
 __global__ void cl_count_kernel(DevState d, int buf)
 {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g < d.n_sites) cl_count_item(d, buf, g);
+    if (g < d.n_sites) cl_count_item(d, buf, g, d.ctr[d.rep_of_site[g]].sweep, d.cell_count);
 }
 
 // Exclusive scan of cell_count into cell_start (n_cells + 1 entries), one

@@ -10,14 +10,14 @@
 
 namespace flipmc {
 
-// Cell of atom g under the sweep's shift; slot by atomic count.  The
-// replica's first atom also publishes the shift.
-__device__ __forceinline__ void cl_count_item(const DevState &d, int buf, int g)
+// Cell of atom g under the shift of sweep `sweep`; slot by atomic count in
+// `counts`.  The replica's first atom also publishes the shift.
+__device__ __forceinline__ void cl_count_item(const DevState &d, int buf, int g, uint64_t sweep, int *counts)
 {
     const int r = d.rep_of_site[g];
     const RepInfo ri = d.rep[r];
     RepCtr *ct = d.ctr + r;
-    const U4 s = rng_block(0xFFFFFFFFu, 0xFFFFFFFFu, ct->sweep, d.par[r].seed);
+    const U4 s = rng_block(0xFFFFFFFFu, 0xFFFFFFFFu, sweep, d.par[r].seed);
     if (g == ri.site_off) {
         ct->shift[0] = s.x;
         ct->shift[1] = s.y;
@@ -27,7 +27,7 @@ __device__ __forceinline__ void cl_count_item(const DevState &d, int buf, int g)
     const int4 rc = d.rec[buf][g];
     const int c = ri.cell_off + cell_local((uint32_t)rc.x, (uint32_t)rc.y, (uint32_t)rc.z, shift, ri.nc);
     d.cell_of[g] = c;
-    d.slot_of[g] = atomicAdd(d.cell_count + c, 1);
+    d.slot_of[g] = atomicAdd(counts + c, 1);
 }
 
 __device__ __forceinline__ void cl_scatter_item(const DevState &d, int buf_in, int buf_out, int g)

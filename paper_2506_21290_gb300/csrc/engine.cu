@@ -532,7 +532,7 @@ int create_impl(mc_handle **out, int n_rep, const double *L, const int32_t *n_mo
         (rc = h->alloc(&h->d_c2, M_tot)) || (rc = h->alloc(&h->d_q, 6 * 256)) ||
         (rc = h->alloc(&h->d_obs_out, 3 * (size_t)n_rep)) ||
         (rc = h->alloc(&h->ds.att_rnd, 2 * (size_t)h->n_sites)) || (rc = h->alloc(&h->d_bar, 2)) ||
-        (rc = h->alloc(&h->ds.cell_done, h->n_cells)) ||
+        (rc = h->alloc(&h->ds.cell_done, h->n_cells)) || (rc = h->alloc(&h->ds.cell_count2, h->n_cells)) ||
         (rc = h->alloc(&h->d_scan_tot, kMaxPersistentBlocks)) ||
         (rc = h->precision == MC_PREC_FP64 ? h->alloc(&h->ds.att_thr64, h->n_sites)
                                            : h->alloc(&h->ds.att_thr32, h->n_sites))) {
@@ -640,7 +640,7 @@ static int sweep_impl(mc_handle *h, int n_sweeps, const double *T, const mc_move
     if (n_sweeps == 0) return MC_OK;
     if (h->pgrid > 0) {
         // all sweeps of the call in one cooperative launch (which expects zero
-        // cell counts on entry and leaves them zero)
+        // counts in cell_count on entry and clears cell_count2 itself)
         CUDA_TRY(cudaMemsetAsync(h->ds.cell_count, 0, sizeof(int) * h->n_cells, h->stream));
         CUDA_TRY(cudaMemsetAsync(h->d_bar, 0, sizeof(unsigned int) * 2, h->stream));
         CUDA_TRY(cudaMemsetAsync(h->ds.cell_done, 0, sizeof(unsigned int) * h->n_cells, h->stream));

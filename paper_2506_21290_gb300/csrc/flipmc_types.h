@@ -98,6 +98,7 @@ struct DevState {
     const int *act_off;  // n_rep + 1 prefix of (nc/2)^3
     int4 *rec[2];        // double-buffered records {qx, qy, qz, w}, cell-sorted
     int *cell_count;
+    int *cell_count2;    // second count buffer (persistent launch: sweep s + 1 is counted while sweep s finishes)
     int *cell_start;     // n_cells + 1
     int *cell_of;
     int *slot_of;

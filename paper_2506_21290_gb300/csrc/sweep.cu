@@ -1480,11 +1480,12 @@ __global__ void __launch_bounds__(BLOCK) finalize_kernel(DevState d)
 
 // ---------------------------------------------------------------------------
 // Persistent sweeps: one cooperative launch runs n_sweeps whole sweeps (cell
-// list, 8 colour phases, finalisation).  The cell-list stages and the
-// finalisation are separated by grid-wide barriers; the colour phases are
-// ordered cell by cell (run_cell).  Every wait is bounded: after a few
-// seconds it records ERR_TIMEOUT and the kernel leaves, instead of waiting
-// forever.
+// list, 8 colour phases, finalisation).  The cell-list stages are separated
+// by grid-wide barriers; the colour phases are ordered cell by cell
+// (run_cell); the finalisation of sweep s shares a stage with the count of
+// sweep s + 1, into the second count buffer, so a sweep takes 6 barriers.
+// Every wait is bounded: after a few seconds it records ERR_TIMEOUT and the
+// kernel leaves, instead of waiting forever.
 // ---------------------------------------------------------------------------
 struct GridBar {
     unsigned int *count;  // arrivals since the launch began (zero at launch)
@@ -1576,14 +1577,22 @@ __global__ void __launch_bounds__(block_threads<W>(), W == 1 ? 3 : 1) sweep_pers
     const int lo = min(nC, (int)blockIdx.x * chunk), hi = min(nC, lo + chunk);
     int buf = buf0;
     unsigned int bar_target = 0;
+    // Every replica of a handle has done the same number of sweeps, so one
+    // base serves all; it is read before any block can reach a finalisation.
+    // Sweep s counts into cell_count for even s, cell_count2 for odd s.
+    __shared__ uint64_t sweep0;
+    if (threadIdx.x == 0) sweep0 = d.ctr[0].sweep;
+    __syncthreads();
+    // ---- cell list of the first sweep: count (cell_count is zero on entry) ----
+    if (n_sweeps > 0)
+        for (int g = tid; g < d.n_sites; g += nthr) cl_count_item(d, buf, g, sweep0, d.cell_count);
     for (int s = 0; s < n_sweeps; ++s) {
-        // ---- cell list: count (cell_count is zero on entry) ----
-        for (int g = tid; g < d.n_sites; g += nthr) cl_count_item(d, buf, g);
+        int *const cnt = (s & 1) ? d.cell_count2 : d.cell_count;
         if (!grid_sync(gb, bar_target, d.err)) return;
         // ---- exclusive scan: chunk totals, then each block scans its chunk ----
         {
             int sum = 0;
-            for (int c = lo + threadIdx.x; c < hi; c += NT) sum += d.cell_count[c];
+            for (int c = lo + threadIdx.x; c < hi; c += NT) sum += cnt[c];
             int total;
             block_excl_scan<NT>(sum, tmp, total);
             if (threadIdx.x == 0) gb.scan_tot[blockIdx.x] = total;
@@ -1602,7 +1611,7 @@ __global__ void __launch_bounds__(block_threads<W>(), W == 1 ? 3 : 1) sweep_pers
             int carry = t1;                       // sum of the totals of earlier blocks
             for (int base = lo; base < hi; base += NT) {
                 const int c = base + threadIdx.x;
-                const int v = c < hi ? d.cell_count[c] : 0;
+                const int v = c < hi ? cnt[c] : 0;
                 int tile;
                 const int ex = block_excl_scan<NT>(v, tmp, tile);
                 if (c < hi) d.cell_start[c] = carry + ex;
@@ -1611,8 +1620,11 @@ __global__ void __launch_bounds__(block_threads<W>(), W == 1 ? 3 : 1) sweep_pers
             if (blockIdx.x == 0 && threadIdx.x == 0) d.cell_start[nC] = t2;
         }
         if (!grid_sync(gb, bar_target, d.err)) return;
-        // ---- scatter, then order each cell and draw its attempts' random numbers ----
+        // ---- scatter (and clear the counts the next sweep will use, last read
+        // by the previous sweep's scan), then order each cell and draw its
+        // attempts' random numbers ----
         for (int g = tid; g < d.n_sites; g += nthr) cl_scatter_item(d, buf, buf ^ 1, g);
+        for (int c = tid; c < nC; c += nthr) ((s & 1) ? d.cell_count : d.cell_count2)[c] = 0;
         if (!grid_sync(gb, bar_target, d.err)) return;
         for (int c = blockIdx.x * (NT / 32) + warp; c < nC; c += gridDim.x * (NT / 32))
             cl_order_cell(d, buf ^ 1, c, lane);
@@ -1623,11 +1635,15 @@ __global__ void __launch_bounds__(block_threads<W>(), W == 1 ? 3 : 1) sweep_pers
             for (int g = blockIdx.x * CPB + gid; g < d.n_act; g += gridDim.x * CPB)
                 run_cell<PREC, W>(d, buf ^ 1, colour, none, g, md, mx, gsmem, gid, (unsigned)s + 1u);
         if (!grid_sync(gb, bar_target, d.err)) return;
-        // ---- finalise the sweep; clear the counts for the next one ----
+        // ---- finalise the sweep and, in the same stage, count the next
+        // sweep's cell list (it reads only the positions written back above,
+        // and the shift of sweep s + 1; the finalisation does not touch the
+        // cell list) ----
         for (int r = blockIdx.x; r < d.n_rep; r += gridDim.x) finalize_replica(d, r, red);
-        for (int c = tid; c < nC; c += nthr) d.cell_count[c] = 0;
-        if (!grid_sync(gb, bar_target, d.err)) return;
         buf ^= 1;
+        if (s + 1 < n_sweeps)
+            for (int g = tid; g < d.n_sites; g += nthr)
+                cl_count_item(d, buf, g, sweep0 + (uint64_t)s + 1u, (s & 1) ? d.cell_count : d.cell_count2);
     }
 }
 
