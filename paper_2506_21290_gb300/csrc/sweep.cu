@@ -63,7 +63,7 @@ __host__ __device__ constexpr int block_threads() { return W > 4 ? 32 * W : BLOC
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int PADS = kPadSlots;     // padding candidates staged after the K atoms
 constexpr int PAD_W = kPadWord;     // their record word: type 0, a molecule no atom has
-constexpr int SCREEN_U = 4;         // 64-candidate steps per screening block
+constexpr int SCREEN_U = 4;         // largest number of 64-candidate steps per screening block
 
 // ---------------------------------------------------------------------------
 // packed FP32 pairs (f32x2, sm_100 and later)
@@ -482,15 +482,33 @@ __device__ __noinline__ void rotate_molecule(const uint32_t (*q)[3], uint32_t (*
 // ---------------------------------------------------------------------------
 // Candidate screens: queue every partner within the screening radius of an
 // old or new position of a moved atom (and, for single-atom moves and flips,
-// every atom of the molecule).  The loads and arithmetic of SCREEN_U steps are
-// issued before any queue store, and the queue is filled in ballot order
-// afterwards.  Lanes past the
-// K staged atoms read the first padding record (no molecule, never within
-// reach), so no lane branches; entries past QW are counted but not stored.
+// every atom of the molecule).  The candidates go in 64-candidate steps: lane
+// l takes candidates base + l and base + 32 + l, so the warp's record loads
+// are contiguous (no shared-memory bank conflicts).  A screening block is U
+// steps (U = 4, and one block of 1 to 3 steps for the rest of the K
+// candidates); the loads and arithmetic of its steps are issued before any
+// queue store, and the queue is filled in ascending candidate order
+// afterwards.  Only the last step of a block can reach past the K staged
+// atoms; its lanes there read the first padding record (no molecule, never
+// within reach), so no lane branches.  Entries past QW are counted but not
+// stored.
 // ---------------------------------------------------------------------------
 
-// append the hits of one 32-candidate step (candidate c = base + lane) in
-// ballot order; lanes without a hit, and hits past QW, write the discard slot
+// append the hits of one 64-candidate step (candidate c = base + lane for bit
+// b0, c + 32 for b1) in ascending candidate order; lanes without a hit, and
+// hits past QW, write the discard slot
+__device__ __forceinline__ void queue_step2(const WarpScr &S, int lane, int &qlen, unsigned b0, unsigned b1, int c)
+{
+    const unsigned lt = (1u << lane) - 1u;
+    const int n0 = __popc(b0);
+    const int e0 = ((b0 >> lane) & 1u) ? min(qlen + __popc(b0 & lt), QW) : QW;
+    const int e1 = ((b1 >> lane) & 1u) ? min(qlen + n0 + __popc(b1 & lt), QW) : QW;
+    S.qc[e0] = c;
+    S.qc[e1] = c + 32;
+    qlen += n0 + __popc(b1);
+}
+
+// append the hits of one 32-candidate step (candidate c = base + lane)
 __device__ __forceinline__ void queue_step(const WarpScr &S, int lane, int &qlen, unsigned b, int c)
 {
     const unsigned lt = (1u << lane) - 1u;
@@ -499,35 +517,52 @@ __device__ __forceinline__ void queue_step(const WarpScr &S, int lane, int &qlen
     qlen += __popc(b);
 }
 
-// append the hits of one 64-candidate step (candidate c = base + 2 lane for
-// bit b0, c + 1 for b1) in ballot order, the same way
-__device__ __forceinline__ void queue_step2(const WarpScr &S, int lane, int &qlen, unsigned b0, unsigned b1, int c)
+// The K candidates in screening blocks: 4 steps while more than 192 remain
+// (only the last step can reach past K), then one block of the 1 to 3 steps
+// that cover the rest.
+template <class Steps>
+__device__ __forceinline__ int screen_blocks(int K, const Steps &st)
 {
-    const unsigned lt = (1u << lane) - 1u;
-    const int e0 = ((b0 >> lane) & 1u) ? min(qlen + __popc(b0 & lt), QW) : QW;
-    const int e1 = ((b1 >> lane) & 1u) ? min(qlen + __popc(b0) + __popc(b1 & lt), QW) : QW;
-    S.qc[e0] = c;
-    S.qc[e1] = c + 1;
-    qlen += __popc(b0) + __popc(b1);
+    int qlen = 0, base = 0;
+    for (; K - base > 64 * (SCREEN_U - 1); base += 64 * SCREEN_U) st.template run<SCREEN_U>(base, qlen);
+    const int rem = (K - base + 63) >> 6;   // 0 to 3
+    if (rem == 3) st.template run<3>(base, qlen);
+    else if (rem == 2) st.template run<2>(base, qlen);
+    else if (rem == 1) st.template run<1>(base, qlen);
+    return qlen;
+}
+
+// candidate pair of step u of a block: below K except in the block's last step
+template <int U>
+__device__ __forceinline__ void step_pair(const Group &G, int K, int base, int u, int lane, int4 &r0, int4 &r1)
+{
+    int c0 = base + 64 * u + lane, c1 = c0 + 32;
+    if (u == U - 1) {
+        c0 = min(c0, K);
+        c1 = min(c1, K);
+    }
+    r0 = G.rec[c0];
+    r1 = G.rec[c1];
 }
 
 // Atom translation from qo to qo + e: the old distance from the exact int32
 // differences, the new one as r'^2 = r^2 - 2 d.e + |e|^2 (fixed-point units);
-// a lane takes two consecutive candidates per step, in packed FP32 pairs.
-__device__ __forceinline__ int screen_atom(const Group &G, const WarpScr &S, int K, int lane, const Q3 &qo,
-                                           const Q3 &qn, int wi, float r2q)
-{
-    const float ex = dq(qn.x, qo.x), ey = dq(qn.y, qo.y), ez = dq(qn.z, qo.z);
-    const f2_t mx = pk(-2.f * ex, -2.f * ex), my = pk(-2.f * ey, -2.f * ey), mz = pk(-2.f * ez, -2.f * ez);
-    const float ee = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-    const f2_t e2 = pk(ee, ee);
-    int qlen = 0;
-    for (int base = 0; base < K; base += 64 * SCREEN_U) {
-        unsigned b0[SCREEN_U], b1[SCREEN_U];
+// the lane's two candidates in packed FP32 pairs.
+struct AtomSteps {
+    const Group &G;
+    const WarpScr &S;
+    int K, lane, wi;
+    Q3 qo;
+    f2_t mx, my, mz, e2;
+    float r2q;
+    template <int U>
+    __device__ __forceinline__ void run(int base, int &qlen) const
+    {
+        unsigned b0[U], b1[U];
 #pragma unroll
-        for (int u = 0; u < SCREEN_U; ++u) {
-            const int c = base + 64 * u + 2 * lane;
-            const int4 r0 = G.rec[c < K ? c : K], r1 = G.rec[c + 1 < K ? c + 1 : K];
+        for (int u = 0; u < U; ++u) {
+            int4 r0, r1;
+            step_pair<U>(G, K, base, u, lane, r0, r1);
             const f2_t X = pk(dq((uint32_t)r0.x, qo.x), dq((uint32_t)r1.x, qo.x));
             const f2_t Y = pk(dq((uint32_t)r0.y, qo.y), dq((uint32_t)r1.y, qo.y));
             const f2_t Z = pk(dq((uint32_t)r0.z, qo.z), dq((uint32_t)r1.z, qo.z));
@@ -542,22 +577,35 @@ __device__ __forceinline__ int screen_atom(const Group &G, const WarpScr &S, int
             b1[u] = __ballot_sync(FULL, p1);
         }
 #pragma unroll
-        for (int u = 0; u < SCREEN_U; ++u) queue_step2(S, lane, qlen, b0[u], b1[u], base + 64 * u + 2 * lane);
+        for (int u = 0; u < U; ++u) queue_step2(S, lane, qlen, b0[u], b1[u], base + 64 * u + lane);
     }
-    return qlen;
+};
+
+__device__ __forceinline__ int screen_atom(const Group &G, const WarpScr &S, int K, int lane, const Q3 &qo,
+                                           const Q3 &qn, int wi, float r2q)
+{
+    const float ex = dq(qn.x, qo.x), ey = dq(qn.y, qo.y), ez = dq(qn.z, qo.z);
+    const float ee = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+    const AtomSteps st{G, S, K, lane, wi, qo, pk(-2.f * ex, -2.f * ex), pk(-2.f * ey, -2.f * ey),
+                       pk(-2.f * ez, -2.f * ez), pk(ee, ee), r2q};
+    return screen_blocks(K, st);
 }
 
 // Flip: distance of every candidate to the two atoms whose types swap.
-__device__ __forceinline__ int screen_flip(const Group &G, const WarpScr &S, int K, int lane, const Q3 &qp,
-                                           const Q3 &qq, int wi, float r2q)
-{
-    int qlen = 0;
-    for (int base = 0; base < K; base += 64 * SCREEN_U) {
-        unsigned b0[SCREEN_U], b1[SCREEN_U];
+struct FlipSteps {
+    const Group &G;
+    const WarpScr &S;
+    int K, lane, wi;
+    Q3 qp, qq;
+    float r2q;
+    template <int U>
+    __device__ __forceinline__ void run(int base, int &qlen) const
+    {
+        unsigned b0[U], b1[U];
 #pragma unroll
-        for (int u = 0; u < SCREEN_U; ++u) {
-            const int c = base + 64 * u + 2 * lane;
-            const int4 r0 = G.rec[c < K ? c : K], r1 = G.rec[c + 1 < K ? c + 1 : K];
+        for (int u = 0; u < U; ++u) {
+            int4 r0, r1;
+            step_pair<U>(G, K, base, u, lane, r0, r1);
             f2_t X = pk(dq((uint32_t)r0.x, qp.x), dq((uint32_t)r1.x, qp.x));
             f2_t Y = pk(dq((uint32_t)r0.y, qp.y), dq((uint32_t)r1.y, qp.y));
             f2_t Z = pk(dq((uint32_t)r0.z, qp.z), dq((uint32_t)r1.z, qp.z));
@@ -575,9 +623,15 @@ __device__ __forceinline__ int screen_flip(const Group &G, const WarpScr &S, int
             b1[u] = __ballot_sync(FULL, p1);
         }
 #pragma unroll
-        for (int u = 0; u < SCREEN_U; ++u) queue_step2(S, lane, qlen, b0[u], b1[u], base + 64 * u + 2 * lane);
+        for (int u = 0; u < U; ++u) queue_step2(S, lane, qlen, b0[u], b1[u], base + 64 * u + lane);
     }
-    return qlen;
+};
+
+__device__ __forceinline__ int screen_flip(const Group &G, const WarpScr &S, int K, int lane, const Q3 &qp,
+                                           const Q3 &qq, int wi, float r2q)
+{
+    const FlipSteps st{G, S, K, lane, wi, qp, qq, r2q};
+    return screen_blocks(K, st);
 }
 
 // Rigid molecule move: the three atoms, old and new (molecule partners are
