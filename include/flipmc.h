@@ -294,11 +294,67 @@ int mc_set_t0(mc_handle *h);
 int mc_observables(mc_handle *h, const double *qvec_atom, int n_qa, const double *qvec_cm, int n_qc,
                    double *out, double *fs_atom, double *fscm_mol, double *c2_mol);
 
-/* Static facts of the handle. */
+/*
+ * Time correlations over many time origins, the statistics of Sec. III.E-F
+ * built on Eq. 5-7.  mc_corr_setup starts a correlation clock t at 0 (the
+ * current state is time 0); from then on t counts the sweeps that
+ * mc_corr_run makes.  At every time t, in this order:
+ *   1. each live origin o with t - t_o = lags[l] adds its per-particle
+ *      correlations at t to the sums of lag l (below), per replica;
+ *   2. an origin with t - t_o >= lags[n_lags-1] stops being live;
+ *   3. if t is a multiple of origin_every and fewer than max_origins origins
+ *      are live, the current state becomes a new origin (the positions, per
+ *      molecule the atom of type B and the orientation u(0), as mc_set_t0),
+ *      and if lags[0] = 0 it adds its lag-0 sample.
+ * lags: n_lags (1..1024) strictly increasing sweep counts >= 0; origin_every
+ * >= 1; max_origins 1..1024; the wavevectors as in mc_observables.  The
+ * origins are kept on the device (3 int64 per site and 4 doubles per
+ * molecule per origin).  A new setup replaces the previous one.
+ * Errors: INVALID_ARG, CUDA (out of device memory).
+ */
+int mc_corr_setup(mc_handle *h, int n_lags, const int64_t *lags, int origin_every, int max_origins,
+                  const double *qvec_atom, int n_qa, const double *qvec_cm, int n_qc);
+
+/*
+ * n_sweeps sweeps (as mc_sweep_batch: the chain is the one that call would
+ * make) with the correlation events of each time on the way.  Sweeps between
+ * two event times run as one launch.  Asynchronous like mc_sweep_batch.
+ * Errors: INVALID_ARG (no setup, bad arguments), CUDA.
+ */
+int mc_corr_run(mc_handle *h, int n_sweeps, const double *T, const mc_move_mix *mix, const uint64_t *seeds);
+
+/*
+ * The raw sums, FP64, sums[(r * n_lags + l) * MC_CORR_NSUM + j] for replica r
+ * and lag l; over the n samples (origins measured at that lag) and, for the
+ * per-particle sums, over the particles of each sample (F_s: the N atoms;
+ * F_s^cm and C_2: the M molecules):
+ *   j = 0: n;
+ *   1, 2: sum of F_s, of F_s^2;     3, 4: sum of fs_i, of fs_i^2;
+ *   5, 6: sum of F_s^cm, of its square;  7, 8: sum of fcm_i, of fcm_i^2;
+ *   9, 10: sum of C_2, of C_2^2;    11, 12: sum of c2_i, of c2_i^2;
+ *   13: sum of c2_i fcm_i;  14, 15: 0.
+ * Sums of replicas at the same state point add.  Synchronous.
+ */
+#define MC_CORR_NSUM 16
+int mc_corr_sums(mc_handle *h, double *sums);
+
+/*
+ * Derived per (replica, lag), out[(r * n_lags + l) * MC_CORR_NRES + j]:
+ *   j = 0: n; 1-3: the averages F_s(q,t), F_s^cm(q,t), C_2(t) (Eq. 5-7);
+ *   4-6: chi_4 = P (<C^2> - <C>^2) of F_s (P = N), F_s^cm and C_2 (P = M)
+ *        (Eq. chi4 of Sec. III.E; <> over the samples);
+ *   7-9: chi_4^self = <C_i^2> - <C_i>^2 of the same three (over particles
+ *        and samples);
+ *   10: the Pearson coefficient of c2_i and fcm_i (Eq. pearson of Sec. III.F).
+ * NaN where n = 0 (and for rho where a variance is 0).  Synchronous.
+ */
+#define MC_CORR_NRES 11
+int mc_corr_results(mc_handle *h, double *out);
+
 /* Pick the cell schedule: run n_sweeps sweeps (>= 1) with each schedule (1,
- * 2 and 4 warps per cell, as one persistent launch per call and as one CUDA
- * graph per sweep) from the same state, time them on the handle's stream and
- * keep the fastest.  The state, the sweep counters, the running energies and
+ * 2, 4 and 8 warps per cell, as one persistent launch per call and as one
+ * CUDA graph per sweep) from the same state, time them on the handle's stream
+ * and keep the fastest.  The state, the sweep counters, the running energies and
  * the statistics are restored afterwards: the chain continues exactly as if
  * the call had not been made (the schedule never changes the chain).  The
  * arguments T, mix and seeds are those of mc_sweep_batch.  results (nullable,
@@ -308,6 +364,7 @@ int mc_observables(mc_handle *h, const double *qvec_atom, int n_qa, const double
 int mc_autotune(mc_handle *h, int n_sweeps, const double *T, const mc_move_mix *mix, const uint64_t *seeds,
                 double *results);
 
+/* Static facts of the handle. */
 int mc_get_info(mc_handle *h, mc_info *info);
 
 /*

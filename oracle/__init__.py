@@ -7,7 +7,8 @@ leg of ``bench.py`` may import this package; the product library never does.
 
 The chain itself lives in ``flipmc_oracle.c`` (built here with
 ``-ffp-contract=off`` so that each FP64 operation rounds once, as written).
-The observables of Sec. III.B (Eq. 5-7) are plain numpy in ``observables.py``.
+The observables of Sec. III.B (Eq. 5-7) are plain numpy in ``observables.py``,
+and their multiple-origin statistics (Sec. III.E-F) in ``correlation.py``.
 """
 from __future__ import annotations
 

@@ -159,6 +159,114 @@ __global__ void observables_kernel(DevState d, const long long *X, ObsState o, c
     c2_mol[m] = 1.5 * x * x - 0.5;
 }
 
+// The per-molecule quantities of one (origin, time) pair that the sums need:
+// F_s of the three atoms (their sum and sum of squares), F_s^cm, C_2, and the
+// products of Eq. chi4 and of the Pearson coefficient.
+struct CorrVals {
+    double v[7];   // sum_k fs_k, sum_k fs_k^2, fcm, fcm^2, c2, c2^2, c2 fcm
+};
+
+__device__ CorrVals corr_molecule(const long long *X, const long long *X0, int kref, const double *u0, int m, double h,
+                                  const double *qa, int nqa, const double *qc, int nqc)
+{
+    double dx[3][3];
+    for (int k = 0; k < 3; ++k)
+        for (int ax = 0; ax < 3; ++ax) dx[k][ax] = (double)(X[9 * (size_t)m + 3 * k + ax] - X0[9 * (size_t)m + 3 * k + ax]) * h;
+    CorrVals o;
+    o.v[0] = 0.0;
+    o.v[1] = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        double s = 0.0;
+        for (int q = 0; q < nqa; ++q)
+            s += cos(qa[3 * q] * dx[k][0] + qa[3 * q + 1] * dx[k][1] + qa[3 * q + 2] * dx[k][2]);
+        const double f = s / (double)nqa;
+        o.v[0] += f;
+        o.v[1] += f * f;
+    }
+    double cm[3];
+    for (int ax = 0; ax < 3; ++ax) cm[ax] = ((dx[0][ax] + dx[1][ax]) + dx[2][ax]) / 3.0;
+    double s = 0.0;
+    for (int q = 0; q < nqc; ++q) s += cos(qc[3 * q] * cm[0] + qc[3 * q + 1] * cm[1] + qc[3 * q + 2] * cm[2]);
+    const double fcm = s / (double)nqc;
+    double u[3];
+    orientation(X, m, kref, h, u);
+    const double x = u[0] * u0[0] + u[1] * u0[1] + u[2] * u0[2];
+    const double c2 = 1.5 * x * x - 0.5;
+    o.v[2] = fcm;
+    o.v[3] = fcm * fcm;
+    o.v[4] = c2;
+    o.v[5] = c2 * c2;
+    o.v[6] = c2 * fcm;
+    return o;
+}
+
+// Block (chunk, pair): the chunk's molecules (one replica's), each thread in
+// ascending order, then a fixed tree over the block's threads.
+__global__ void __launch_bounds__(256) corr_chunk_kernel(DevState d, const long long *X, CorrDev c, CorrPairs p)
+{
+    const int chunk = blockIdx.x, pr = blockIdx.y;
+    const int m0 = c.chunk_m0[chunk], m1 = c.chunk_m0[chunk + 1];
+    const int slot = p.slot[pr];
+    const size_t M = c.n_sites / 3;
+    const long long *X0 = c.X0 + (size_t)slot * 3 * c.n_sites;
+    const int *kref = c.kref + (size_t)slot * M;
+    const double *u0 = c.u0 + (size_t)slot * 3 * M;
+    const double h = d.rep[d.rep_of_site[3 * m0]].h;
+    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (int m = m0 + threadIdx.x; m < m1; m += 256) {
+        const CorrVals v = corr_molecule(X, X0, kref[m], u0 + 3 * (size_t)m, m, h, c.qa, c.n_qa, c.qc, c.n_qc);
+        for (int j = 0; j < 7; ++j) acc[j] = __dadd_rn(acc[j], v.v[j]);
+    }
+    __shared__ double red[7][256];
+    for (int j = 0; j < 7; ++j) red[j][threadIdx.x] = acc[j];
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            for (int j = 0; j < 7; ++j) red[j][threadIdx.x] = __dadd_rn(red[j][threadIdx.x], red[j][threadIdx.x + w]);
+        __syncthreads();
+    }
+    if (threadIdx.x < 7) c.partials[((size_t)pr * c.n_chunks + chunk) * kCorrPart + threadIdx.x] = red[threadIdx.x][0];
+}
+
+// Thread (pair, replica): the replica's chunk sums in chunk order, then the
+// sample's contribution to the replica's accumulators of the pair's lag.
+// Different origins never share a lag at one time, so each accumulator has
+// one writer per launch.
+__global__ void corr_finish_kernel(DevState d, CorrDev c, CorrPairs p)
+{
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= p.n * d.n_rep) return;
+    const int pr = idx / d.n_rep, r = idx - pr * d.n_rep;
+    double S[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (int k = c.rep_chunk0[r]; k < c.rep_chunk0[r + 1]; ++k)
+        for (int j = 0; j < 7; ++j) S[j] = __dadd_rn(S[j], c.partials[((size_t)pr * c.n_chunks + k) * kCorrPart + j]);
+    const double M = (double)(d.rep[r].n_sites / 3), N = 3.0 * M;
+    const double fs = S[0] / N, fcm = S[2] / M, c2 = S[4] / M;
+    double *a = c.acc + ((size_t)r * c.n_lags + p.lag[pr]) * MC_CORR_NSUM;
+    a[0] += 1.0;
+    a[1] += fs;
+    a[2] += fs * fs;
+    a[3] += S[0];
+    a[4] += S[1];
+    a[5] += fcm;
+    a[6] += fcm * fcm;
+    a[7] += S[2];
+    a[8] += S[3];
+    a[9] += c2;
+    a[10] += c2 * c2;
+    a[11] += S[4];
+    a[12] += S[5];
+    a[13] += S[6];
+}
+
+void launch_corr_sample(const DevState &d, const long long *X, const CorrDev &c, const CorrPairs &p, cudaStream_t st)
+{
+    if (p.n <= 0) return;
+    corr_chunk_kernel<<<dim3(c.n_chunks, p.n), 256, 0, st>>>(d, X, c, p);
+    const int n = p.n * d.n_rep;
+    corr_finish_kernel<<<(n + 127) / 128, 128, 0, st>>>(d, c, p);
+}
+
 void launch_gather(const DevState &d, int buf, long long *X, int *types, cudaStream_t st)
 {
     gather_kernel<<<(d.n_sites + 255) / 256, 256, 0, st>>>(d, buf, X, types);

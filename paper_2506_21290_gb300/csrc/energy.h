@@ -24,4 +24,37 @@ void launch_observables(const DevState &d, const long long *X, const ObsState &o
                         const double *qc, int nqc, double *fs_site, double *fscm_mol, double *c2_mol, double *out,
                         cudaStream_t st);
 
+// Multiple-origin correlations: the origins live in slots; each slot holds an
+// ObsState's arrays (slot s at X0 + 3 N s, kref + M s, u0 + 3 M s).
+struct CorrDev {
+    const long long *X0;
+    const int *kref;
+    const double *u0;
+    size_t n_sites;             // all replicas
+    const double *qa;           // n_qa wavevectors (atoms), 3 each
+    const double *qc;           // n_qc wavevectors (centres of mass)
+    int n_qa, n_qc;
+    const int *chunk_m0;        // per chunk: first molecule (global index), chunk_m0[n_chunks] = total molecules
+    int n_chunks;
+    const int *rep_chunk0;      // per replica: first chunk; [n_rep] = n_chunks
+    double *partials;           // CORR_PART per (pair, chunk)
+    double *acc;                // MC_CORR_NSUM per (replica, lag)
+    int n_lags;
+};
+
+constexpr int kCorrMaxPairs = 32;       // (origin, lag) pairs per launch
+constexpr int kCorrChunk = 1024;        // molecules per block of the per-particle pass
+constexpr int kCorrPart = 8;            // partial sums per (pair, chunk)
+
+// The (origin slot, lag index) pairs measured at one time.
+struct CorrPairs {
+    int n;
+    int slot[kCorrMaxPairs];
+    int lag[kCorrMaxPairs];
+};
+
+// Per-particle correlations of each pair against the current unwrapped
+// positions X, summed per replica into the accumulators (fixed order).
+void launch_corr_sample(const DevState &d, const long long *X, const CorrDev &c, const CorrPairs &p, cudaStream_t st);
+
 }  // namespace flipmc

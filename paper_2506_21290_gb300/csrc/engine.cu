@@ -87,6 +87,16 @@ struct mc_handle {
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     DevState ds{};
     ObsState obs{};
+    // multiple-origin correlations (mc_corr_*)
+    struct Corr {
+        bool on = false;
+        std::vector<long long> lags;
+        int every = 1;
+        long long t = 0;                  // correlation clock: sweeps made by mc_corr_run since the setup
+        std::vector<long long> slot_t0;   // origin time per slot, -1: free
+        std::vector<void *> bufs;         // device buffers of the setup
+        CorrDev dev{};
+    } corr;
     std::vector<Buf> allocs;
     // device scratch
     RepInfo *d_rep = nullptr;
@@ -608,11 +618,20 @@ int mc_create_batch(mc_handle **out, int n_rep, const double *L, const int32_t *
     return create_impl(out, n_rep, L, n_mol, xyz, types, params, opts);
 }
 
+// Release the buffers of a correlation setup (after the stream is idle).
+static void corr_free(mc_handle *h)
+{
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    for (void *b : h->corr.bufs) cudaFree(b);
+    h->corr = mc_handle::Corr{};
+}
+
 void mc_destroy(mc_handle *h)
 {
     if (!h) return;
     cudaSetDevice(h->device);
     if (h->stream) cudaStreamSynchronize(h->stream);
+    corr_free(h);
     for (int b = 0; b < 2; ++b)
         if (h->graph[b]) cudaGraphExecDestroy(h->graph[b]);
     for (auto &a : h->allocs) cudaFree(a.p);
@@ -1029,6 +1048,233 @@ int mc_observables(mc_handle *h, const double *qvec_atom, int n_qa, const double
     if (fscm_mol) CUDA_TRY(cudaMemcpyAsync(fscm_mol, h->d_fscm, sizeof(double) * M, cudaMemcpyDeviceToHost, h->stream));
     if (c2_mol) CUDA_TRY(cudaMemcpyAsync(c2_mol, h->d_c2, sizeof(double) * M, cudaMemcpyDeviceToHost, h->stream));
     CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return MC_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Multiple-origin correlations
+// ---------------------------------------------------------------------------
+namespace {
+
+template <class T>
+int corr_alloc(mc_handle *h, T **p, size_t n)
+{
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, std::max<size_t>(n, 1) * sizeof(T));
+    if (e != cudaSuccess) return fail(MC_ERR_CUDA, std::string("cudaMalloc (correlation origins): ") + cudaGetErrorString(e));
+    h->corr.bufs.push_back(q);
+    *p = (T *)q;
+    return MC_OK;
+}
+
+ObsState corr_slot(const mc_handle *h, int s)
+{
+    const size_t N = (size_t)h->n_sites, M = N / 3;
+    ObsState o;
+    o.X0 = const_cast<long long *>(h->corr.dev.X0) + (size_t)s * 3 * N;
+    o.kref = const_cast<int *>(h->corr.dev.kref) + (size_t)s * M;
+    o.u0 = const_cast<double *>(h->corr.dev.u0) + (size_t)s * 3 * M;
+    return o;
+}
+
+// The events of the current time t: samples of the live origins whose lag
+// has come, retirement of origins past the last lag, a new origin.
+int corr_events(mc_handle *h)
+{
+    auto &c = h->corr;
+    const long long t = c.t;
+    bool gathered = false;
+    CorrPairs p{};
+    auto gather = [&]() {
+        if (!gathered) launch_gather(h->ds, h->cur, h->d_X, h->d_types, h->stream);
+        gathered = true;
+    };
+    auto flush = [&]() {
+        if (p.n > 0) {
+            gather();
+            launch_corr_sample(h->ds, h->d_X, c.dev, p, h->stream);
+        }
+        p.n = 0;
+    };
+    const int n_slots = (int)c.slot_t0.size();
+    for (int s = 0; s < n_slots; ++s) {
+        if (c.slot_t0[s] < 0) continue;
+        const auto it = std::lower_bound(c.lags.begin(), c.lags.end(), t - c.slot_t0[s]);
+        if (it == c.lags.end() || *it != t - c.slot_t0[s]) continue;
+        p.slot[p.n] = s;
+        p.lag[p.n] = (int)(it - c.lags.begin());
+        if (++p.n == kCorrMaxPairs) flush();
+    }
+    flush();
+    for (int s = 0; s < n_slots; ++s)
+        if (c.slot_t0[s] >= 0 && t - c.slot_t0[s] >= c.lags.back()) c.slot_t0[s] = -1;
+    if (t % c.every == 0) {
+        int s = 0;
+        while (s < n_slots && c.slot_t0[s] >= 0) ++s;
+        if (s < n_slots) {
+            gather();
+            launch_set_t0(h->ds, h->d_X, h->d_types, corr_slot(h, s), h->stream);
+            c.slot_t0[s] = t;
+            if (c.lags[0] == 0) {
+                p.slot[0] = s;
+                p.lag[0] = 0;
+                p.n = 1;
+                flush();
+            }
+        }
+    }
+    CUDA_TRY(cudaGetLastError());
+    return MC_OK;
+}
+
+// The next time after t with an event: a multiple of origin_every, or a live
+// origin's next lag.
+long long corr_next(const mc_handle::Corr &c)
+{
+    long long nxt = (c.t / c.every + 1) * c.every;
+    for (const long long t0 : c.slot_t0) {
+        if (t0 < 0) continue;
+        const auto it = std::upper_bound(c.lags.begin(), c.lags.end(), c.t - t0);
+        if (it != c.lags.end()) nxt = std::min(nxt, t0 + *it);
+    }
+    return nxt;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mc_corr_setup(mc_handle *h, int n_lags, const int64_t *lags, int origin_every, int max_origins,
+                  const double *qvec_atom, int n_qa, const double *qvec_cm, int n_qc)
+{
+    if (!h || !lags || !qvec_atom || !qvec_cm) return fail(MC_ERR_INVALID_ARG, "NULL argument");
+    if (n_lags < 1 || n_lags > 1024) return fail(MC_ERR_INVALID_ARG, "1 <= n_lags <= 1024");
+    for (int l = 0; l < n_lags; ++l)
+        if (lags[l] < 0 || (l > 0 && lags[l] <= lags[l - 1]))
+            return fail(MC_ERR_INVALID_ARG, "lags must be strictly increasing and >= 0");
+    if (origin_every < 1) return fail(MC_ERR_INVALID_ARG, "origin_every >= 1");
+    if (max_origins < 1 || max_origins > 1024) return fail(MC_ERR_INVALID_ARG, "1 <= max_origins <= 1024");
+    if (n_qa < 1 || n_qa > 256 || n_qc < 1 || n_qc > 256) return fail(MC_ERR_INVALID_ARG, "1 <= n_q <= 256");
+    int rc = set_device(h);
+    if (rc) return rc;
+    corr_free(h);
+    auto &c = h->corr;
+    const size_t N = (size_t)h->n_sites, M = N / 3;
+    // chunks of at most kCorrChunk molecules, none spanning two replicas
+    std::vector<int> chunk_m0, rep_chunk0;
+    for (int r = 0; r < h->n_rep; ++r) {
+        rep_chunk0.push_back((int)chunk_m0.size());
+        const int m_off = h->reps[r].site_off / 3, m_n = h->reps[r].n_sites / 3;
+        for (int m = 0; m < m_n; m += kCorrChunk) chunk_m0.push_back(m_off + m);
+    }
+    const int n_chunks = (int)chunk_m0.size();
+    rep_chunk0.push_back(n_chunks);
+    chunk_m0.push_back((int)M);
+    long long *X0 = nullptr;
+    int *kref = nullptr, *cm0 = nullptr, *rc0 = nullptr;
+    double *u0 = nullptr, *q = nullptr, *part = nullptr, *acc = nullptr;
+    const size_t n_acc = (size_t)h->n_rep * n_lags * MC_CORR_NSUM;
+    if ((rc = corr_alloc(h, &X0, (size_t)max_origins * 3 * N)) || (rc = corr_alloc(h, &kref, (size_t)max_origins * M)) ||
+        (rc = corr_alloc(h, &u0, (size_t)max_origins * 3 * M)) || (rc = corr_alloc(h, &q, 3 * (size_t)(n_qa + n_qc))) ||
+        (rc = corr_alloc(h, &cm0, chunk_m0.size())) || (rc = corr_alloc(h, &rc0, rep_chunk0.size())) ||
+        (rc = corr_alloc(h, &part, (size_t)kCorrMaxPairs * n_chunks * kCorrPart)) || (rc = corr_alloc(h, &acc, n_acc))) {
+        corr_free(h);
+        return rc;
+    }
+    CUDA_TRY(cudaMemcpy(q, qvec_atom, sizeof(double) * 3 * n_qa, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(q + 3 * n_qa, qvec_cm, sizeof(double) * 3 * n_qc, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(cm0, chunk_m0.data(), sizeof(int) * chunk_m0.size(), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(rc0, rep_chunk0.data(), sizeof(int) * rep_chunk0.size(), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemset(acc, 0, sizeof(double) * n_acc));
+    c.dev.X0 = X0;
+    c.dev.kref = kref;
+    c.dev.u0 = u0;
+    c.dev.n_sites = N;
+    c.dev.qa = q;
+    c.dev.qc = q + 3 * n_qa;
+    c.dev.n_qa = n_qa;
+    c.dev.n_qc = n_qc;
+    c.dev.chunk_m0 = cm0;
+    c.dev.n_chunks = n_chunks;
+    c.dev.rep_chunk0 = rc0;
+    c.dev.partials = part;
+    c.dev.acc = acc;
+    c.dev.n_lags = n_lags;
+    c.lags.assign(lags, lags + n_lags);
+    c.every = origin_every;
+    c.t = 0;
+    c.slot_t0.assign(max_origins, -1);
+    c.on = true;
+    return corr_events(h);
+}
+
+int mc_corr_run(mc_handle *h, int n_sweeps, const double *T, const mc_move_mix *mix, const uint64_t *seeds)
+{
+    if (!h) return fail(MC_ERR_INVALID_ARG, "NULL handle");
+    if (!h->corr.on) return fail(MC_ERR_INVALID_ARG, "mc_corr_setup has not been called");
+    if (n_sweeps < 0 || !T || !mix || !seeds) return fail(MC_ERR_INVALID_ARG, "bad arguments");
+    int left = n_sweeps;
+    while (left > 0) {
+        const long long nxt = corr_next(h->corr);
+        const int k = (int)std::min<long long>(left, nxt - h->corr.t);
+        int rc = sweep_impl(h, k, T, mix, seeds, false);
+        if (rc) return rc;
+        h->corr.t += k;
+        left -= k;
+        if (h->corr.t == nxt && (rc = corr_events(h))) return rc;
+    }
+    return MC_OK;
+}
+
+int mc_corr_sums(mc_handle *h, double *sums)
+{
+    if (!h || !sums) return fail(MC_ERR_INVALID_ARG, "NULL argument");
+    if (!h->corr.on) return fail(MC_ERR_INVALID_ARG, "mc_corr_setup has not been called");
+    int rc = set_device(h);
+    if (rc) return rc;
+    const size_t n = (size_t)h->n_rep * h->corr.lags.size() * MC_CORR_NSUM;
+    CUDA_TRY(cudaMemcpyAsync(sums, h->corr.dev.acc, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return MC_OK;
+}
+
+int mc_corr_results(mc_handle *h, double *out)
+{
+    if (!h || !out) return fail(MC_ERR_INVALID_ARG, "NULL argument");
+    if (!h->corr.on) return fail(MC_ERR_INVALID_ARG, "mc_corr_setup has not been called");
+    const int nl = (int)h->corr.lags.size();
+    std::vector<double> S((size_t)h->n_rep * nl * MC_CORR_NSUM);
+    int rc = mc_corr_sums(h, S.data());
+    if (rc) return rc;
+    const double nan = std::nan("");
+    for (int r = 0; r < h->n_rep; ++r) {
+        const double N = (double)h->reps[r].n_sites, M = N / 3.0;
+        for (int l = 0; l < nl; ++l) {
+            const double *a = S.data() + ((size_t)r * nl + l) * MC_CORR_NSUM;
+            double *o = out + ((size_t)r * nl + l) * MC_CORR_NRES;
+            const double n = a[0];
+            o[0] = n;
+            if (!(n > 0.0)) {
+                for (int j = 1; j < MC_CORR_NRES; ++j) o[j] = nan;
+                continue;
+            }
+            const double fs = a[1] / n, fcm = a[5] / n, c2 = a[9] / n;
+            o[1] = fs;
+            o[2] = fcm;
+            o[3] = c2;
+            o[4] = N * (a[2] / n - fs * fs);
+            o[5] = M * (a[6] / n - fcm * fcm);
+            o[6] = M * (a[10] / n - c2 * c2);
+            const double fs_i = a[3] / (n * N), fcm_i = a[7] / (n * M), c2_i = a[11] / (n * M);
+            o[7] = a[4] / (n * N) - fs_i * fs_i;
+            o[8] = a[8] / (n * M) - fcm_i * fcm_i;
+            o[9] = a[12] / (n * M) - c2_i * c2_i;
+            const double den = o[9] * o[8];
+            o[10] = den > 0.0 ? (a[13] / (n * M) - c2_i * fcm_i) / std::sqrt(den) : nan;
+        }
+    }
     return MC_OK;
 }
 

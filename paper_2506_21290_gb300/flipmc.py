@@ -106,6 +106,10 @@ def load():
         "mc_set_t0": ([vp], i32),
         "mc_observables": ([vp, vp, i32, vp, i32, vp, vp, vp, vp], i32),
         "mc_get_info": ([vp, vp], i32),
+        "mc_corr_setup": ([vp, i32, vp, i32, i32, vp, i32, vp, i32], i32),
+        "mc_corr_run": ([vp, i32, vp, vp, vp], i32),
+        "mc_corr_sums": ([vp, vp], i32),
+        "mc_corr_results": ([vp, vp], i32),
         "mc_last_error": ([], C.c_char_p),
         "mc_energy_noalloc": ([dbl, i32, vp, vp, vp, vp, vp], i32),
     }
@@ -292,6 +296,39 @@ def mc_observables(h, qa, qc, n_rep, total_sites, per_particle=False):
     return out, fs, fscm, c2
 
 
+MC_CORR_NSUM = 16
+MC_CORR_NRES = 11
+CORR_RESULT_FIELDS = ("n", "F_s", "F_s_cm", "C_2", "chi4_F_s", "chi4_F_s_cm", "chi4_C_2", "chi4self_F_s",
+                      "chi4self_F_s_cm", "chi4self_C_2", "rho")
+
+
+def mc_corr_setup(h, lags, origin_every, max_origins, qa, qc):
+    lags = np.ascontiguousarray(lags, dtype=np.int64).reshape(-1)
+    qa = np.ascontiguousarray(qa, dtype=np.float64).reshape(-1, 3)
+    qc = np.ascontiguousarray(qc, dtype=np.float64).reshape(-1, 3)
+    _check(load().mc_corr_setup(h, len(lags), _ptr(lags), int(origin_every), int(max_origins), _ptr(qa), len(qa),
+                                _ptr(qc), len(qc)), "mc_corr_setup")
+
+
+def mc_corr_run(h, n, T, mix, seeds):
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    seeds = np.ascontiguousarray(seeds, dtype=np.uint64)
+    m = make_mix(mix)
+    _check(load().mc_corr_run(h, int(n), _ptr(T), C.byref(m), _ptr(seeds)), "mc_corr_run")
+
+
+def mc_corr_sums(h, n_rep, n_lags):
+    out = np.zeros((n_rep, n_lags, MC_CORR_NSUM), dtype=np.float64)
+    _check(load().mc_corr_sums(h, _ptr(out)), "mc_corr_sums")
+    return out
+
+
+def mc_corr_results(h, n_rep, n_lags):
+    out = np.zeros((n_rep, n_lags, MC_CORR_NRES), dtype=np.float64)
+    _check(load().mc_corr_results(h, _ptr(out)), "mc_corr_results")
+    return out
+
+
 def mc_get_info(h):
     i = mc_info()
     _check(load().mc_get_info(h, C.byref(i)), "mc_get_info")
@@ -398,6 +435,23 @@ class Handle:
 
     def observables(self, qa, qc, per_particle=False):
         return mc_observables(self.h, qa, qc, self.n_rep, self.N, per_particle)
+
+    def corr_setup(self, lags, origin_every, max_origins, qa, qc):
+        """Multiple-origin correlations from the current state (time 0)."""
+        self._corr_lags = len(np.asarray(lags).reshape(-1))
+        mc_corr_setup(self.h, lags, origin_every, max_origins, qa, qc)
+
+    def corr_run(self, n, T, mix, seed):
+        Ts = np.broadcast_to(np.asarray(T, dtype=np.float64), (self.n_rep,))
+        seeds = np.broadcast_to(np.asarray(seed, dtype=np.uint64), (self.n_rep,))
+        mc_corr_run(self.h, n, Ts, mix, seeds)
+
+    def corr_sums(self):
+        return mc_corr_sums(self.h, self.n_rep, self._corr_lags)
+
+    def corr_results(self):
+        """(n_rep, n_lags, 11): see CORR_RESULT_FIELDS."""
+        return mc_corr_results(self.h, self.n_rep, self._corr_lags)
 
     def stats(self):
         return mc_state_stats(self.h, self.n_rep)

@@ -1,0 +1,156 @@
+"""GPU parity of the multiple-origin correlations (mc_corr_*) with the oracle.
+
+The library and the oracle run the same chain (FP64 mode is bit-exact; FP32
+mode takes the same decisions), so the positions at every sample are equal
+and the per-particle correlations differ only by FP64 rounding (CUDA's cos
+against numpy's, and the order of the sums).  The raw sums are compared to
+1e-12 relative to their scale, the derived statistics to matching bounds.
+The library's reductions run in a fixed order, so splitting a run into calls
+changes no bit.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import correlation as OC
+from paper_2506_21290_gb300 import flipmc as F
+from paper_2506_21290_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+POT = W.PAPER_POT
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2506_21290_gb300 import build as B
+    B.build()
+    oracle.build()
+
+
+def _qvecs(qmag, n, seed):
+    v = np.random.default_rng(seed).normal(size=(n, 3))
+    return qmag * v / np.linalg.norm(v, axis=1, keepdims=True)
+
+
+QA, QC = _qvecs(7.4, 12, 1), _qvecs(5.1, 8, 2)
+
+
+def _start(M, seed):
+    L = W.box_length(M)
+    xyz, t = W.lattice_start(M, L, seed)
+    return L, xyz, t
+
+
+def _compare(sums_gpu, res_gpu, corr):
+    so, ro = corr.sums(), corr.results()
+    assert np.array_equal(sums_gpu[:, 0], so[:, 0])                       # sample counts
+    scale = np.maximum(np.abs(so), 1.0)
+    assert np.all(np.abs(sums_gpu - so) <= 1e-12 * scale), np.max(np.abs(sums_gpu - so) / scale)
+    has = so[:, 0] > 0
+    assert np.all(np.isnan(res_gpu[~has, 1:]))
+    assert np.allclose(res_gpu[has, 1:4], ro[has, 1:4], rtol=0, atol=1e-12)
+    # chi_4 = P (<C^2> - <C>^2): a difference of sums of size ~1, times P
+    N = corr.ch.t.size
+    assert np.allclose(res_gpu[has, 4:7], ro[has, 4:7], rtol=0, atol=1e-10 * N)
+    assert np.allclose(res_gpu[has, 7:10], ro[has, 7:10], rtol=0, atol=1e-10)
+    ok = has & np.isfinite(ro[:, 10])
+    assert np.allclose(res_gpu[ok, 10], ro[ok, 10], rtol=0, atol=1e-8)
+
+
+@pytest.mark.parametrize("M,prec,T,seed", [(64, "fp64", 2.0, 3), (125, "fp32", 1.1, 4)])
+def test_corr_matches_oracle(M, prec, T, seed):
+    L, xyz, t = _start(M, seed)
+    lags = [0, 1, 2, 3, 5, 8, 13]
+    h = F.Handle(L, xyz, t, POT, precision=prec)
+    ch = oracle.Chain(L, xyz, t, POT, nc=h.info["max_cells_per_axis"])
+    h.corr_setup(lags, 2, 5, QA, QC)
+    oc = OC.Correlator(ch, lags, 2, 5, QA, QC)
+    h.corr_run(40, T, W.PAPER_MIX, 50 + seed)
+    oc.run(40, T, W.PAPER_MIX, 50 + seed)
+    q, X, tt = h.state_fixed()
+    assert np.array_equal(q, ch.q) and np.array_equal(X, ch.X) and np.array_equal(tt, ch.t)
+    _compare(h.corr_sums()[0], h.corr_results()[0], oc)
+
+
+def _cells_per_axis(L):
+    # the library's choice: the largest even n_c whose cells are >= 1.575 wide
+    n = 2
+    while np.floor(2 ** 32 / (n + 2)) * L / 2 ** 32 >= 1.575:
+        n += 2
+    return n
+
+
+def test_corr_batch_of_replicas():
+    """Replicas of different size and temperature, each against its own oracle chain."""
+    Ms, Ts, seeds = [64, 125], [3.0, 1.5], [11, 12]
+    Ls = [W.box_length(m) for m in Ms]
+    starts = [W.lattice_start(m, l, s) for m, l, s in zip(Ms, Ls, seeds)]
+    h = F.Handle(np.array(Ls), np.concatenate([s[0] for s in starts]), np.concatenate([s[1] for s in starts]), POT,
+                 precision="fp32", n_mol=np.array(Ms))
+    lags = [0, 2, 4, 6]
+    h.corr_setup(lags, 3, 4, QA, QC)
+    cs = []
+    for r in range(2):
+        ch = oracle.Chain(Ls[r], starts[r][0], starts[r][1], POT, nc=_cells_per_axis(Ls[r]))
+        cs.append(OC.Correlator(ch, lags, 3, 4, QA, QC))
+    h.corr_run(25, np.array(Ts), W.PAPER_MIX, np.array(seeds, dtype=np.uint64))
+    for r in range(2):
+        cs[r].run(25, Ts[r], W.PAPER_MIX, seeds[r])
+    S, R = h.corr_sums(), h.corr_results()
+    for r in range(2):
+        _compare(S[r], R[r], cs[r])
+
+
+def test_corr_split_calls_and_chain_unchanged():
+    L, xyz, t = _start(216, 6)
+    lags = [0, 1, 4, 9, 16]
+    a = F.Handle(L, xyz, t, POT, precision="fp32")
+    b = F.Handle(L, xyz, t, POT, precision="fp32")
+    c = F.Handle(L, xyz, t, POT, precision="fp32")
+    for h in (a, b):
+        h.corr_setup(lags, 3, 6, QA, QC)
+    a.corr_run(37, 1.2, W.PAPER_MIX, 9)
+    for n in (5, 1, 12, 19):
+        b.corr_run(n, 1.2, W.PAPER_MIX, 9)
+    c.sweep(37, 1.2, W.PAPER_MIX, 9)
+    assert np.array_equal(a.corr_sums(), b.corr_sums())        # bit for bit
+    for h in (b, c):
+        for u, v in zip(a.state_fixed(), h.state_fixed()):
+            assert np.array_equal(u, v)
+
+
+def test_corr_lag_zero_and_counts_at_full_size():
+    """M = 8000: lag 0 gives exactly 1 for F_s and F_s^cm, 1 to rounding for
+    C_2, and no fluctuation; the sample counts follow the schedule."""
+    spec = W.WORKLOADS["single-8000"]
+    L = W.box_length(spec["M"])
+    xyz, t = W.lattice_start(spec["M"], L, spec["seed"])
+    h = F.Handle(L, xyz, t, POT, precision="fp32")
+    lags = [0, 10, 20]
+    h.corr_setup(lags, 10, 3, QA, QC)
+    h.corr_run(50, spec["T"], W.PAPER_MIX, spec["seed"])
+    R = h.corr_results()[0]
+    assert R[:, 0].tolist() == [6, 5, 4]          # origins at 0, 10, ..., 50
+    assert R[0, 1] == 1.0 and R[0, 2] == 1.0
+    assert R[0, 3] == pytest.approx(1.0, abs=1e-13)
+    assert abs(R[0, 4]) < 1e-9 and abs(R[0, 7]) < 1e-15
+    assert np.all(R[1:, 1] < 1.0) and np.all(R[1:, 3] < 1.0)
+
+
+def test_corr_slot_limit_and_bad_arguments():
+    L, xyz, t = _start(64, 7)
+    h = F.Handle(L, xyz, t, POT, precision="fp32")
+    h.corr_setup([0, 5], 1, 1, QA, QC)
+    h.corr_run(12, 2.0, W.PAPER_MIX, 1)
+    # one slot: origins at 0, 5, 10 (each frees its slot at its last lag)
+    assert h.corr_results()[0][:, 0].tolist() == [3, 2]
+    for bad in (dict(lags=[3, 3]), dict(lags=[-1, 2]), dict(every=0), dict(max_o=0), dict(max_o=2000)):
+        kw = dict(lags=[0, 2], every=1, max_o=4)
+        kw.update(bad)
+        with pytest.raises(F.McError) as e:
+            h.corr_setup(kw["lags"], kw["every"], kw["max_o"], QA, QC)
+        assert e.value.code == F.MC_ERR_INVALID_ARG
+    fresh = F.Handle(L, xyz, t, POT, precision="fp32")
+    with pytest.raises(F.McError):
+        fresh.corr_run(1, 2.0, W.PAPER_MIX, 1)
