@@ -64,6 +64,9 @@ def parse():
                     help="sweeps per schedule for mc_autotune when the schedule is automatic (0: off)")
     ap.add_argument("--one-by-one", type=int, default=16,
                     help="batched workloads: replicas timed one by one on their own handles (0: off)")
+    ap.add_argument("--corr", type=int, default=0,
+                    help="also time the multiple-origin correlation sampling with this many origins "
+                         "measured per event (0: off)")
     return ap.parse_args()
 
 
@@ -250,6 +253,43 @@ def run_one_by_one(F, wl, mix, sps, n_take, precision):
             "sweeps_each": sps, "what": "the same replicas, own handle each, one after the other"}
 
 
+def run_corr(h, wl, mix, P, stream, n_events=10):
+    """Cost of one correlation event with P (origin, lag) pairs over the whole
+    state: lags 0..P-1, an origin every sweep, so that every sweep after the
+    first P ends in an event of exactly P pairs.  Each timed sweep with its
+    event is compared with the same sweep alone."""
+    import torch
+    rng = np.random.default_rng(2506)
+    qa, qc = rng.normal(size=(12, 3)), rng.normal(size=(8, 3))
+    qa *= 7.4 / np.linalg.norm(qa, axis=1, keepdims=True)
+    qc *= 5.1 / np.linalg.norm(qc, axis=1, keepdims=True)
+    h.corr_setup(np.arange(P), 1, P, qa, qc)
+    h.corr_run(P + 2, wl["T"], mix, wl["seeds"])
+
+    def timed(fn):
+        tot = 0.0
+        for _ in range(n_events):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            tot += a.elapsed_time(b)
+        return tot / n_events
+
+    with_ev = timed(lambda: h.corr_run(1, wl["T"], mix, wl["seeds"]))
+    plain = timed(lambda: h.sweep(1, wl["T"], mix, wl["seeds"]))
+    M = h.N // 3
+    ev_ms = max(with_ev - plain, 1e-6)
+    cos_per_pair = 3 * len(qa) + len(qc)
+    return {"pairs_per_event": P, "event_ms": ev_ms, "sweep_plus_event_ms": with_ev, "sweep_ms": plain,
+            "molecule_samples_per_s": P * M / (ev_ms * 1e-3),
+            "fp64_cos_per_s": P * M * cos_per_pair / (ev_ms * 1e-3),
+            "what": "per event: gather of the unwrapped positions, F_s (12 q), F_s^cm (8 q), C_2 per molecule "
+                    "for each pair in FP64, fixed-order per-replica sums, one new origin"}
+
+
 def run_native(args):
     import torch
     from paper_2506_21290_gb300 import build as B
@@ -419,6 +459,8 @@ def run_native(args):
         "gpu_launches": args.steps * ((1 + 1) if persistent else sps * launches_per_sweep) + args.steps * 2,
         "clocks": clk,
     }
+    if args.corr > 0:
+        line["corr"] = run_corr(h, wl, mix, args.corr, stream)
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.barrier()

@@ -228,18 +228,27 @@ __global__ void __launch_bounds__(256) corr_chunk_kernel(DevState d, const long 
     if (threadIdx.x < 7) c.partials[((size_t)pr * c.n_chunks + chunk) * kCorrPart + threadIdx.x] = red[threadIdx.x][0];
 }
 
-// Thread (pair, replica): the replica's chunk sums in chunk order, then the
+// Block (pair, replica): the replica's chunk sums (thread k takes chunks k,
+// k + 128, ... in order, then a fixed tree over the threads), then the
 // sample's contribution to the replica's accumulators of the pair's lag.
 // Different origins never share a lag at one time, so each accumulator has
 // one writer per launch.
-__global__ void corr_finish_kernel(DevState d, CorrDev c, CorrPairs p)
+__global__ void __launch_bounds__(128) corr_finish_kernel(DevState d, CorrDev c, CorrPairs p)
 {
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= p.n * d.n_rep) return;
-    const int pr = idx / d.n_rep, r = idx - pr * d.n_rep;
+    const int pr = blockIdx.x / d.n_rep, r = blockIdx.x - pr * d.n_rep;
     double S[7] = {0, 0, 0, 0, 0, 0, 0};
-    for (int k = c.rep_chunk0[r]; k < c.rep_chunk0[r + 1]; ++k)
+    for (int k = c.rep_chunk0[r] + threadIdx.x; k < c.rep_chunk0[r + 1]; k += 128)
         for (int j = 0; j < 7; ++j) S[j] = __dadd_rn(S[j], c.partials[((size_t)pr * c.n_chunks + k) * kCorrPart + j]);
+    __shared__ double red[7][128];
+    for (int j = 0; j < 7; ++j) red[j][threadIdx.x] = S[j];
+    __syncthreads();
+    for (int w = 64; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            for (int j = 0; j < 7; ++j) red[j][threadIdx.x] = __dadd_rn(red[j][threadIdx.x], red[j][threadIdx.x + w]);
+        __syncthreads();
+    }
+    if (threadIdx.x != 0) return;
+    for (int j = 0; j < 7; ++j) S[j] = red[j][0];
     const double M = (double)(d.rep[r].n_sites / 3), N = 3.0 * M;
     const double fs = S[0] / N, fcm = S[2] / M, c2 = S[4] / M;
     double *a = c.acc + ((size_t)r * c.n_lags + p.lag[pr]) * MC_CORR_NSUM;
@@ -263,8 +272,7 @@ void launch_corr_sample(const DevState &d, const long long *X, const CorrDev &c,
 {
     if (p.n <= 0) return;
     corr_chunk_kernel<<<dim3(c.n_chunks, p.n), 256, 0, st>>>(d, X, c, p);
-    const int n = p.n * d.n_rep;
-    corr_finish_kernel<<<(n + 127) / 128, 128, 0, st>>>(d, c, p);
+    corr_finish_kernel<<<p.n * d.n_rep, 128, 0, st>>>(d, c, p);
 }
 
 void launch_gather(const DevState &d, int buf, long long *X, int *types, cudaStream_t st)

@@ -43,7 +43,7 @@ struct CorrDev {
 };
 
 constexpr int kCorrMaxPairs = 32;       // (origin, lag) pairs per launch
-constexpr int kCorrChunk = 1024;        // molecules per block of the per-particle pass
+constexpr int kCorrChunk = 256;         // molecules per block of the per-particle pass (one per thread)
 constexpr int kCorrPart = 8;            // partial sums per (pair, chunk)
 
 // The (origin slot, lag index) pairs measured at one time.
