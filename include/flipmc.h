@@ -223,6 +223,39 @@ int mc_sync(mc_handle *h);
 int mc_energy(mc_handle *h, double *E_out);
 
 /*
+ * Pressure of each replica from the virial (Sec. II.C quotes P = 30 at T = 1,
+ * rho = 1.2): out[2r] = W, the sum over all pairs i < j of -r dphi/dr (the
+ * derivative of Eq. 1 and, for the three bonds of a molecule, Eq. 2), FP64
+ * over the cell neighbourhoods; out[2r+1] = N T[r] / V + W / (3 V) with N
+ * the replica's atoms and V = L^3.  T: n_rep temperatures (host).
+ * Synchronous.  Errors: INVALID_ARG (NULL, T <= 0), CUDA.
+ */
+int mc_pressure(mc_handle *h, const double *T, double *out);
+
+/*
+ * Static structure factor of the atoms (Sec. IV.A, Eq. sq):
+ * out[r * n_q + k] = |sum_i exp(i q_k . x_i)|^2 / N per replica r and
+ * wavevector qvec[3k..3k+2], over the N atoms of the replica at their wrapped
+ * positions x in [0, L)^3, FP64.  This is the double sum of Eq. sq with the
+ * i = j terms (each 1) included; the sum over i != j alone is out - 1.  Use
+ * wavevectors of the reciprocal lattice, q = 2 pi n / L, for which the result
+ * does not depend on the periodic image.  1 <= n_q <= 65535.  Synchronous.
+ */
+int mc_structure_factor(mc_handle *h, const double *qvec, int n_q, double *out);
+
+/*
+ * Pair-distance histogram of the atoms (Sec. IV.A, Eq. gr): counts[r * n_bins
+ * + b] = the number of pairs i < j of replica r whose minimum-image distance
+ * r_ij satisfies floor(r_ij / dr) = b, with r_ij from the int32 fixed-point
+ * differences in FP64 (each product and sum rounded once, x then y then z,
+ * then sqrt, then the division).  g (nullable, n_rep * n_bins doubles) gets
+ * g(r) = 2 counts / (N rho V_shell) with rho = N / V and V_shell the volume of
+ * the bin's spherical shell.  0 < dr, 1 <= n_bins <= 4096, n_bins dr <= L / 2
+ * for every replica.  Synchronous.  Errors: INVALID_ARG, CUDA.
+ */
+int mc_pair_histogram(mc_handle *h, double dr, int n_bins, uint64_t *counts, double *g);
+
+/*
  * As mc_energy, but only enqueued on the handle's stream: dev_E_out is a
  * device buffer of n_rep doubles owned by the caller (for example a torch
  * tensor).  No synchronisation; errors surface at the next mc_sync.

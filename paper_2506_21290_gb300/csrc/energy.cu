@@ -6,9 +6,11 @@
 
 namespace flipmc {
 
-// Energy of every atom i with its partners j > i (site index) in the 27 (or 8)
-// neighbour cells; pairs beyond every cutoff are screened in FP32 and add 0.
-__global__ void energy_sites_kernel(DevState d, int buf, double *e_site)
+// Energy (VIRIAL = false) or pair virial (VIRIAL = true) of every atom i with
+// its partners j > i (site index) in the 27 (or 8) neighbour cells; pairs
+// beyond every cutoff are screened in FP32 and add 0.
+template <bool VIRIAL>
+__global__ void pair_sites_kernel(DevState d, int buf, double *e_site)
 {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= d.n_sites) return;
@@ -50,7 +52,8 @@ __global__ void energy_sites_kernel(DevState d, int buf, double *e_site)
                 if (fx * fx + fy * fy + fz * fz > pre) continue;
             }
             const double r2 = r2_fixed64(dx, dy, dz, ri.h);
-            e = __dadd_rn(e, phi64(md, r2, 3 * ti + rec_type(o.w), bonded));
+            const int ab = 3 * ti + rec_type(o.w);
+            e = __dadd_rn(e, VIRIAL ? virial64(md, r2, ab, bonded) : phi64(md, r2, ab, bonded));
         }
     }
     e_site[ri.site_off + si] = e;
@@ -78,8 +81,14 @@ __global__ void __launch_bounds__(256) replica_sum_kernel(DevState d, const doub
 
 void launch_energy(const DevState &d, int buf, double *e_site, double *e_out_dev, cudaStream_t st)
 {
-    energy_sites_kernel<<<(d.n_sites + 255) / 256, 256, 0, st>>>(d, buf, e_site);
+    pair_sites_kernel<false><<<(d.n_sites + 255) / 256, 256, 0, st>>>(d, buf, e_site);
     replica_sum_kernel<<<d.n_rep, 256, 0, st>>>(d, e_site, 0, 0.0, e_out_dev, 1, 0);
+}
+
+void launch_virial(const DevState &d, int buf, double *w_site, double *w_out_dev, cudaStream_t st)
+{
+    pair_sites_kernel<true><<<(d.n_sites + 255) / 256, 256, 0, st>>>(d, buf, w_site);
+    replica_sum_kernel<<<d.n_rep, 256, 0, st>>>(d, w_site, 0, 0.0, w_out_dev, 1, 0);
 }
 
 // Unwrapped fixed-point positions and types in site-index order.
@@ -273,6 +282,92 @@ void launch_corr_sample(const DevState &d, const long long *X, const CorrDev &c,
     if (p.n <= 0) return;
     corr_chunk_kernel<<<dim3(c.n_chunks, p.n), 256, 0, st>>>(d, X, c, p);
     corr_finish_kernel<<<p.n * d.n_rep, 128, 0, st>>>(d, c, p);
+}
+
+// S(q) of one (replica, wavevector) per block: the sums of cos and sin of
+// q . x over the replica's atoms (x = q_fixed h, in [0, L)), each thread in
+// ascending order, then a fixed tree; out = (C^2 + S^2) / N (Eq. sq with the
+// i = j terms included).
+__global__ void __launch_bounds__(256) sq_kernel(DevState d, const long long *X, const double *qv, int n_q,
+                                                 double *out)
+{
+    const int r = blockIdx.y, k = blockIdx.x;
+    const RepInfo ri = d.rep[r];
+    const double qx = qv[3 * k], qy = qv[3 * k + 1], qz = qv[3 * k + 2];
+    double c = 0.0, sn = 0.0;
+    for (int i = threadIdx.x; i < ri.n_sites; i += 256) {
+        const long long *x = X + 3 * (size_t)(ri.site_off + i);
+        const double ph = qx * ((double)(uint32_t)x[0] * ri.h) + qy * ((double)(uint32_t)x[1] * ri.h) +
+                          qz * ((double)(uint32_t)x[2] * ri.h);
+        double sv, cv;
+        sincos(ph, &sv, &cv);
+        c = __dadd_rn(c, cv);
+        sn = __dadd_rn(sn, sv);
+    }
+    __shared__ double rc[256], rs[256];
+    rc[threadIdx.x] = c;
+    rs[threadIdx.x] = sn;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            rc[threadIdx.x] = __dadd_rn(rc[threadIdx.x], rc[threadIdx.x + w]);
+            rs[threadIdx.x] = __dadd_rn(rs[threadIdx.x], rs[threadIdx.x + w]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[(size_t)r * n_q + k] = (rc[0] * rc[0] + rs[0] * rs[0]) / (double)ri.n_sites;
+}
+
+void launch_sq(const DevState &d, const long long *X, const double *qv, int n_q, double *out, cudaStream_t st)
+{
+    sq_kernel<<<dim3(n_q, d.n_rep), 256, 0, st>>>(d, X, qv, n_q, out);
+}
+
+// Pair-distance histogram of one replica (Eq. gr): every pair once, by the
+// ring order: thread i takes the pairs (i, i + k mod N) for k = 1 .. (N-1)/2,
+// and for even N the pair (i, i + N/2) when i < N/2.  Bin = floor(r / dr)
+// with r from the FP64 minimum-image distance (each operation rounded once,
+// in a fixed order), counted when below n_bins.
+__global__ void __launch_bounds__(128) pair_hist_kernel(DevState d, const long long *X, double dr, int n_bins,
+                                                        unsigned long long *counts)
+{
+    extern __shared__ unsigned int hist[];
+    const int r = blockIdx.y;
+    const RepInfo ri = d.rep[r];
+    const int N = ri.n_sites;
+    for (int b = threadIdx.x; b < n_bins; b += 128) hist[b] = 0;
+    __syncthreads();
+    const int i = blockIdx.x * 128 + threadIdx.x;
+    if (blockIdx.x * 128 < N) {
+        const double rmax = dr * (double)n_bins;
+        const double guard2 = rmax * rmax * (1.0 + 1e-12);
+        const int half = (N - 1) / 2;
+        const bool extra = (N % 2 == 0) && i < N / 2;
+        if (i < N) {
+            const long long *xi = X + 3 * (size_t)(ri.site_off + i);
+            const uint32_t ax = (uint32_t)xi[0], ay = (uint32_t)xi[1], az = (uint32_t)xi[2];
+            for (int k = 1; k <= half + (extra ? 1 : 0); ++k) {
+                int j = i + k;
+                if (j >= N) j -= N;
+                const long long *xj = X + 3 * (size_t)(ri.site_off + j);
+                const double r2 = r2_fixed64((int)((uint32_t)xj[0] - ax), (int)((uint32_t)xj[1] - ay),
+                                             (int)((uint32_t)xj[2] - az), ri.h);
+                if (!(r2 < guard2)) continue;
+                const int bin = (int)floor(__ddiv_rn(__dsqrt_rn(r2), dr));
+                if (bin < n_bins) atomicAdd(&hist[bin], 1u);
+            }
+        }
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < n_bins; b += 128)
+        if (hist[b]) atomicAdd(counts + (size_t)r * n_bins + b, (unsigned long long)hist[b]);
+}
+
+void launch_pair_hist(const DevState &d, const long long *X, int max_sites, double dr, int n_bins,
+                      unsigned long long *counts, cudaStream_t st)
+{
+    pair_hist_kernel<<<dim3((max_sites + 127) / 128, d.n_rep), 128, sizeof(unsigned int) * n_bins, st>>>(
+        d, X, dr, n_bins, counts);
 }
 
 void launch_gather(const DevState &d, int buf, long long *X, int *types, cudaStream_t st)

@@ -16,6 +16,13 @@ struct ObsState {
 
 // FP64 energy per replica into e_out_dev[n_rep]; e_site is n_sites scratch.
 void launch_energy(const DevState &d, int buf, double *e_site, double *e_out_dev, cudaStream_t st);
+// S(q) per (replica, wavevector): out[r * n_q + k] = |sum_i exp(i q_k . x_i)|^2 / N.
+void launch_sq(const DevState &d, const long long *X, const double *qv, int n_q, double *out, cudaStream_t st);
+// Pair-distance counts per replica and bin (every pair once); counts zeroed by the caller.
+void launch_pair_hist(const DevState &d, const long long *X, int max_sites, double dr, int n_bins,
+                      unsigned long long *counts, cudaStream_t st);
+// FP64 pair virial sum W = sum_{i<j} -r dphi/dr per replica into w_out_dev[n_rep].
+void launch_virial(const DevState &d, int buf, double *w_site, double *w_out_dev, cudaStream_t st);
 // unwrapped positions (3 per site) and types in site order
 void launch_gather(const DevState &d, int buf, long long *X, int *types, cudaStream_t st);
 void launch_set_t0(const DevState &d, const long long *X, const int *types, const ObsState &o, cudaStream_t st);

@@ -873,6 +873,93 @@ int mc_energy(mc_handle *h, double *E_out)
     return check_device_errors(h);
 }
 
+int mc_pressure(mc_handle *h, const double *T, double *out)
+{
+    if (!h || !T || !out) return fail(MC_ERR_INVALID_ARG, "NULL argument");
+    for (int r = 0; r < h->n_rep; ++r)
+        if (!(T[r] > 0.0) || !std::isfinite(T[r])) return fail(MC_ERR_INVALID_ARG, "temperature must be positive");
+    int rc = set_device(h);
+    if (rc) return rc;
+    launch_virial(h->ds, h->cur, h->d_e_site, h->d_e_out, h->stream);
+    CUDA_TRY(cudaGetLastError());
+    std::vector<double> w(h->n_rep);
+    CUDA_TRY(cudaMemcpyAsync(w.data(), h->d_e_out, sizeof(double) * h->n_rep, cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    for (int r = 0; r < h->n_rep; ++r) {
+        const double V = h->reps[r].L * h->reps[r].L * h->reps[r].L;
+        out[2 * r] = w[r];
+        out[2 * r + 1] = (double)h->reps[r].n_sites * T[r] / V + w[r] / (3.0 * V);
+    }
+    return check_device_errors(h);
+}
+
+int mc_structure_factor(mc_handle *h, const double *qvec, int n_q, double *out)
+{
+    if (!h || !qvec || !out) return fail(MC_ERR_INVALID_ARG, "NULL argument");
+    if (n_q < 1 || n_q > 65535) return fail(MC_ERR_INVALID_ARG, "1 <= n_q <= 65535");
+    int rc = set_device(h);
+    if (rc) return rc;
+    double *dq = nullptr, *dout = nullptr;
+    CUDA_TRY(cudaMallocAsync(&dq, sizeof(double) * 3 * n_q, h->stream));
+    CUDA_TRY(cudaMallocAsync(&dout, sizeof(double) * (size_t)n_q * h->n_rep, h->stream));
+    cudaError_t e = cudaMemcpyAsync(dq, qvec, sizeof(double) * 3 * n_q, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) {
+        launch_gather(h->ds, h->cur, h->d_X, h->d_types, h->stream);
+        launch_sq(h->ds, h->d_X, dq, n_q, dout, h->stream);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out, dout, sizeof(double) * (size_t)n_q * h->n_rep, cudaMemcpyDeviceToHost, h->stream);
+    cudaFreeAsync(dq, h->stream);
+    cudaFreeAsync(dout, h->stream);
+    const cudaError_t e2 = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess || e2 != cudaSuccess)
+        return fail(MC_ERR_CUDA, std::string("structure factor: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+    return check_device_errors(h);
+}
+
+int mc_pair_histogram(mc_handle *h, double dr, int n_bins, uint64_t *counts, double *g)
+{
+    if (!h || !counts) return fail(MC_ERR_INVALID_ARG, "NULL argument");
+    if (!(dr > 0.0) || !std::isfinite(dr) || n_bins < 1 || n_bins > 4096)
+        return fail(MC_ERR_INVALID_ARG, "dr > 0 and 1 <= n_bins <= 4096");
+    int max_sites = 0;
+    for (auto &r : h->reps) {
+        if (dr * n_bins > 0.5 * r.L) return fail(MC_ERR_INVALID_ARG, "n_bins * dr exceeds half a box side");
+        max_sites = std::max(max_sites, r.n_sites);
+    }
+    int rc = set_device(h);
+    if (rc) return rc;
+    const size_t n = (size_t)n_bins * h->n_rep;
+    unsigned long long *dc = nullptr;
+    CUDA_TRY(cudaMallocAsync(&dc, sizeof(unsigned long long) * n, h->stream));
+    cudaError_t e = cudaMemsetAsync(dc, 0, sizeof(unsigned long long) * n, h->stream);
+    if (e == cudaSuccess) {
+        launch_gather(h->ds, h->cur, h->d_X, h->d_types, h->stream);
+        launch_pair_hist(h->ds, h->d_X, max_sites, dr, n_bins, dc, h->stream);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(counts, dc, sizeof(unsigned long long) * n, cudaMemcpyDeviceToHost, h->stream);
+    cudaFreeAsync(dc, h->stream);
+    const cudaError_t e2 = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess || e2 != cudaSuccess)
+        return fail(MC_ERR_CUDA, std::string("pair histogram: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+    if (g) {
+        // g(r) at the bin centres: 2 counts / (N rho shell volume), rho = N / V
+        const double pi = 3.14159265358979323846;
+        for (int r = 0; r < h->n_rep; ++r) {
+            const double N = (double)h->reps[r].n_sites, V = h->reps[r].L * h->reps[r].L * h->reps[r].L;
+            for (int b = 0; b < n_bins; ++b) {
+                const double r0 = b * dr, r1 = (b + 1) * dr;
+                const double shell = 4.0 / 3.0 * pi * (r1 * r1 * r1 - r0 * r0 * r0);
+                g[(size_t)r * n_bins + b] = 2.0 * (double)counts[(size_t)r * n_bins + b] / (N * (N / V) * shell);
+            }
+        }
+    }
+    return check_device_errors(h);
+}
+
 static int fetch_records(mc_handle *h, std::vector<int4> &rec, std::vector<int> &img)
 {
     rec.resize(h->n_sites);

@@ -129,6 +129,24 @@ __device__ __forceinline__ double phi64(const ModelDev &md, double r2, int ab, b
     return u;
 }
 
+// Pair virial -r dphi/dr in FP64 (the derivative of Eq. 1 and Eq. 2):
+// WCA 24 eps s6 (2 s6 - 1) inside the cutoff (s6 = (sigma^2/r^2)^3), and for a
+// bond FENE -2 K eps x / (1 - x) with x = r^2 / (R0 sigma)^2.
+__device__ __forceinline__ double virial64(const ModelDev &md, double r2, int ab, bool bonded)
+{
+    double w = 0.0;
+    if (r2 < md.rc2[ab]) {
+        const double t = __ddiv_rn(md.s2[ab], r2);
+        const double s6 = __dmul_rn(__dmul_rn(t, t), t);
+        w = __dmul_rn(__dmul_rn(6.0, md.e4), __dmul_rn(s6, __dsub_rn(__dmul_rn(2.0, s6), 1.0)));
+    }
+    if (bonded) {
+        const double x = __ddiv_rn(r2, md.R2[ab]);
+        w = __dadd_rn(w, __dmul_rn(__dmul_rn(2.0, md.nke), __ddiv_rn(x, __dsub_rn(1.0, x))));
+    }
+    return w;
+}
+
 // FP32 WCA with its magnitude 4eps s12 + 4eps s6 + eps (the FP32 error scale).
 __device__ __forceinline__ void wca32(const ModelDev &md, float r2, int ab, float &u, float &mag)
 {

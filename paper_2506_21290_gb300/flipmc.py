@@ -106,6 +106,9 @@ def load():
         "mc_set_t0": ([vp], i32),
         "mc_observables": ([vp, vp, i32, vp, i32, vp, vp, vp, vp], i32),
         "mc_get_info": ([vp, vp], i32),
+        "mc_pressure": ([vp, vp, vp], i32),
+        "mc_structure_factor": ([vp, vp, i32, vp], i32),
+        "mc_pair_histogram": ([vp, dbl, i32, vp, vp], i32),
         "mc_corr_setup": ([vp, i32, vp, i32, i32, vp, i32, vp, i32], i32),
         "mc_corr_run": ([vp, i32, vp, vp, vp], i32),
         "mc_corr_sums": ([vp, vp], i32),
@@ -296,6 +299,27 @@ def mc_observables(h, qa, qc, n_rep, total_sites, per_particle=False):
     return out, fs, fscm, c2
 
 
+def mc_pressure(h, T):
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    out = np.zeros((T.size, 2), dtype=np.float64)
+    _check(load().mc_pressure(h, _ptr(T), _ptr(out)), "mc_pressure")
+    return out
+
+
+def mc_structure_factor(h, qvec, n_rep):
+    qvec = np.ascontiguousarray(qvec, dtype=np.float64).reshape(-1, 3)
+    out = np.zeros((n_rep, len(qvec)), dtype=np.float64)
+    _check(load().mc_structure_factor(h, _ptr(qvec), len(qvec), _ptr(out)), "mc_structure_factor")
+    return out
+
+
+def mc_pair_histogram(h, dr, n_bins, n_rep):
+    counts = np.zeros((n_rep, n_bins), dtype=np.uint64)
+    g = np.zeros((n_rep, n_bins), dtype=np.float64)
+    _check(load().mc_pair_histogram(h, float(dr), int(n_bins), _ptr(counts), _ptr(g)), "mc_pair_histogram")
+    return counts, g
+
+
 MC_CORR_NSUM = 16
 MC_CORR_NRES = 11
 CORR_RESULT_FIELDS = ("n", "F_s", "F_s_cm", "C_2", "chi4_F_s", "chi4_F_s_cm", "chi4_C_2", "chi4self_F_s",
@@ -435,6 +459,18 @@ class Handle:
 
     def observables(self, qa, qc, per_particle=False):
         return mc_observables(self.h, qa, qc, self.n_rep, self.N, per_particle)
+
+    def pressure(self, T):
+        """(n_rep, 2): the pair virial sum W and the pressure N T / V + W / (3 V)."""
+        return mc_pressure(self.h, np.broadcast_to(np.asarray(T, dtype=np.float64), (self.n_rep,)))
+
+    def structure_factor(self, qvec):
+        """(n_rep, n_q): |sum_i exp(i q . x_i)|^2 / N."""
+        return mc_structure_factor(self.h, qvec, self.n_rep)
+
+    def pair_histogram(self, dr, n_bins):
+        """(counts, g): pair-distance counts per bin (pairs i < j) and g(r), each (n_rep, n_bins)."""
+        return mc_pair_histogram(self.h, dr, n_bins, self.n_rep)
 
     def corr_setup(self, lags, origin_every, max_origins, qa, qc):
         """Multiple-origin correlations from the current state (time 0)."""
