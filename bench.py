@@ -41,7 +41,7 @@ L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) per launch of the dominant kernel from the ncu capture summarised in
 # profiles/sweep_persistent_single-1000_full.md; keyed by (workload, kernel, sweeps per launch), so a timed
 # launch that differs from the captured one reports null
-NCU_TRAFFIC = {("single-1000", "sweep_persistent<FP32,W=4>", 100): 233472}
+NCU_TRAFFIC = {("single-1000", "sweep_persistent<FP32,W=4>", 100): 267776}
 
 
 def parse():
