@@ -384,6 +384,17 @@ int mc_corr_sums(mc_handle *h, double *sums);
 #define MC_CORR_NRES 11
 int mc_corr_results(mc_handle *h, double *out);
 
+/*
+ * Relaxation time per replica (Sec. III.C: the time at which a correlation
+ * function reaches e^-1): the first lag l (in increasing order, lags with no
+ * sample skipped) at which the average of which = 0 (F_s), 1 (F_s^cm) or
+ * 2 (C_2) is <= level, interpolated linearly in ln t from the previous lag
+ * (linearly in t when that lag is 0), or lags[l] itself when it is the first
+ * lag sampled.  tau[n_rep] (host); NaN where the series stays above level.
+ * Synchronous.  Errors: INVALID_ARG (no setup, which out of range).
+ */
+int mc_corr_relaxation_time(mc_handle *h, int which, double level, double *tau);
+
 /* Pick the cell schedule: run n_sweeps sweeps (>= 1) with each schedule (1,
  * 2, 4 and 8 warps per cell, as one persistent launch per call and as one
  * CUDA graph per sweep) from the same state, time them on the handle's stream

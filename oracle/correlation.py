@@ -120,3 +120,22 @@ def stats_of_samples(ss):
     if pooled[1].var() > 0 and pooled[2].var() > 0:
         out[10] = np.corrcoef(pooled[2], pooled[1])[0, 1]
     return out
+
+
+def relaxation_time(lags, series, counts, level):
+    """The time at which a lag series first reaches level (Sec. III.C, level
+    e^-1): lags without samples are skipped; between the bracketing lags the
+    crossing is placed linearly in ln t (linearly in t from lag 0); the first
+    sampled lag itself when the series starts at or below level; NaN if it
+    never crosses."""
+    pts = [(float(t), float(f)) for t, f, n in zip(lags, series, counts) if n > 0]
+    for k, (t, f) in enumerate(pts):
+        if f <= level:
+            if k == 0:
+                return t
+            t0, f0 = pts[k - 1]
+            a = (f0 - level) / (f0 - f)
+            if t0 > 0:
+                return float(np.exp(np.log(t0) + a * (np.log(t) - np.log(t0))))
+            return t0 + a * (t - t0)
+    return float("nan")

@@ -1365,6 +1365,44 @@ int mc_corr_results(mc_handle *h, double *out)
     return MC_OK;
 }
 
+int mc_corr_relaxation_time(mc_handle *h, int which, double level, double *tau)
+{
+    if (!h || !tau) return fail(MC_ERR_INVALID_ARG, "NULL argument");
+    if (which < 0 || which > 2) return fail(MC_ERR_INVALID_ARG, "which: 0 F_s, 1 F_s^cm, 2 C_2");
+    if (!h->corr.on) return fail(MC_ERR_INVALID_ARG, "mc_corr_setup has not been called");
+    const auto &lags = h->corr.lags;
+    const int nl = (int)lags.size();
+    std::vector<double> R((size_t)h->n_rep * nl * MC_CORR_NRES);
+    int rc = mc_corr_results(h, R.data());
+    if (rc) return rc;
+    for (int r = 0; r < h->n_rep; ++r) {
+        tau[r] = std::nan("");
+        double t_prev = 0.0, f_prev = 0.0;
+        bool have_prev = false;
+        for (int l = 0; l < nl; ++l) {
+            const double *o = R.data() + ((size_t)r * nl + l) * MC_CORR_NRES;
+            if (!(o[0] > 0.0)) continue;               // no sample at this lag
+            const double t = (double)lags[l], f = o[1 + which];
+            if (f <= level) {
+                if (!have_prev) {
+                    tau[r] = t;
+                } else if (t_prev > 0.0) {
+                    // linear in ln t between the two lags that bracket the crossing
+                    const double a = (f_prev - level) / (f_prev - f);
+                    tau[r] = std::exp(std::log(t_prev) + a * (std::log(t) - std::log(t_prev)));
+                } else {
+                    tau[r] = t_prev + (f_prev - level) / (f_prev - f) * (t - t_prev);
+                }
+                break;
+            }
+            t_prev = t;
+            f_prev = f;
+            have_prev = true;
+        }
+    }
+    return MC_OK;
+}
+
 int mc_get_info(mc_handle *h, mc_info *info)
 {
     if (!h || !info) return fail(MC_ERR_INVALID_ARG, "NULL argument");

@@ -113,6 +113,7 @@ def load():
         "mc_corr_run": ([vp, i32, vp, vp, vp], i32),
         "mc_corr_sums": ([vp, vp], i32),
         "mc_corr_results": ([vp, vp], i32),
+        "mc_corr_relaxation_time": ([vp, i32, dbl, vp], i32),
         "mc_last_error": ([], C.c_char_p),
         "mc_energy_noalloc": ([dbl, i32, vp, vp, vp, vp, vp], i32),
     }
@@ -353,6 +354,12 @@ def mc_corr_results(h, n_rep, n_lags):
     return out
 
 
+def mc_corr_relaxation_time(h, which, level, n_rep):
+    tau = np.zeros(n_rep, dtype=np.float64)
+    _check(load().mc_corr_relaxation_time(h, int(which), float(level), _ptr(tau)), "mc_corr_relaxation_time")
+    return tau
+
+
 def mc_get_info(h):
     i = mc_info()
     _check(load().mc_get_info(h, C.byref(i)), "mc_get_info")
@@ -488,6 +495,10 @@ class Handle:
     def corr_results(self):
         """(n_rep, n_lags, 11): see CORR_RESULT_FIELDS."""
         return mc_corr_results(self.h, self.n_rep, self._corr_lags)
+
+    def corr_relaxation_time(self, which=0, level=float(np.exp(-1.0))):
+        """Per replica: the time at which F_s (0), F_s^cm (1) or C_2 (2) reaches level."""
+        return mc_corr_relaxation_time(self.h, which, level, self.n_rep)
 
     def stats(self):
         return mc_state_stats(self.h, self.n_rep)

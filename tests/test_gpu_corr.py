@@ -71,6 +71,13 @@ def test_corr_matches_oracle(M, prec, T, seed):
     q, X, tt = h.state_fixed()
     assert np.array_equal(q, ch.q) and np.array_equal(X, ch.X) and np.array_equal(tt, ch.t)
     _compare(h.corr_sums()[0], h.corr_results()[0], oc)
+    # relaxation times (Sec. III.C) from the library against the oracle's series, at levels the series cross
+    ro = oc.results()
+    for which in (0, 1, 2):
+        for level in (0.98, 0.9, float(np.exp(-1.0))):
+            want = OC.relaxation_time(lags, ro[:, 1 + which], ro[:, 0], level)
+            got = h.corr_relaxation_time(which, level)[0]
+            assert (np.isnan(want) and np.isnan(got)) or got == pytest.approx(want, rel=1e-9), (which, level)
 
 
 def _cells_per_axis(L):
@@ -154,3 +161,19 @@ def test_corr_slot_limit_and_bad_arguments():
     fresh = F.Handle(L, xyz, t, POT, precision="fp32")
     with pytest.raises(F.McError):
         fresh.corr_run(1, 2.0, W.PAPER_MIX, 1)
+
+
+def test_flip_moves_speed_up_relaxation_more_as_T_drops():
+    """Sec. III.C-D: tau_alpha (F_s at q = 7.4 reaching e^-1) of flip MC against
+    local MC (translations only).  Measured with 8 replicas: 913 vs 1200 sweeps
+    at T = 2.5, 1637 vs 2774 at T = 2.0, 3396 vs 10142 at T = 1.6.  Here 4
+    replicas at the two higher temperatures: local MC is slower at both, and
+    more so at the lower one."""
+    from paper_2506_21290_gb300 import speedup as SP
+    ratio = {}
+    for T, lag_max in ((2.5, 2000), (2.0, 5000)):
+        tf = SP.measure(T, W.PAPER_MIX, 1000, 4, lag_max, lag_max, 3 * lag_max, seed=200)["tau_alpha"]
+        tl = SP.measure(T, W.LOCAL_MIX, 1000, 4, lag_max, lag_max, 3 * lag_max, seed=200)["tau_alpha"]
+        ratio[T] = tl / tf
+    print("tau_local / tau_flip:", ratio)
+    assert ratio[2.5] > 1.1 and ratio[2.0] > ratio[2.5] + 0.15

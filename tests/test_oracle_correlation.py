@@ -165,3 +165,20 @@ def test_sample_counts_two_slots():
     # 0 frees at 9 and the next origin starts at 10, then 12, ... (period 10)
     starts = [t for k in range(6) for t in (10 * k, 10 * k + 2)]
     assert _counts([1, 4, 9], 2, 2, 50) == _want([t for t in starts if t <= 50], [1, 4, 9], 50)
+
+
+def test_relaxation_time_interpolation():
+    lags = [0, 1, 10, 100, 1000]
+    # a series linear in ln t crosses exactly where the line does
+    f = [1.0, 0.9, 0.9 - 0.3 * np.log(10), 0.9 - 0.3 * np.log(100), 0.9 - 0.3 * np.log(1000)]
+    level = 0.5
+    want = np.exp((0.9 - level) / 0.3)
+    assert OC.relaxation_time(lags, f, [1] * 5, level) == pytest.approx(want, rel=1e-12)
+    # crossing between lag 0 and lag 1: linear in t
+    assert OC.relaxation_time([0, 1], [1.0, 0.0], [1, 1], 0.25) == pytest.approx(0.75, rel=1e-12)
+    # a crossing exactly at a lag point, lags without samples skipped, never crossing
+    assert OC.relaxation_time(lags, [1, 0.8, np.exp(-1), 0.1, 0.0], [1] * 5, np.exp(-1)) == pytest.approx(10.0, rel=1e-12)
+    # lag 1 has no sample: the crossing lies between lag 0 and lag 10, linear in t
+    assert OC.relaxation_time(lags, [1, 0.2, 0.1, 0.05, 0.0], [1, 0, 1, 1, 1], 0.3) == pytest.approx(
+        10 * 0.7 / 0.9, rel=1e-12)
+    assert np.isnan(OC.relaxation_time(lags, [1, 0.9, 0.8, 0.7, 0.6], [1] * 5, 0.5))
