@@ -395,6 +395,30 @@ int mc_corr_results(mc_handle *h, double *out);
  */
 int mc_corr_relaxation_time(mc_handle *h, int which, double level, double *tau);
 
+/*
+ * Molecular dynamics of the same model (Sec. II.D: NVT, time step 0.001,
+ * Nose-Hoover thermostat with relaxation time 1), FP64, m = 1.  One step is
+ * the symmetric splitting
+ *   xi += dt/2 (2K - gT)/Q; eta += dt/2 xi; v *= exp(-xi dt/2); v += dt/2 F;
+ *   q += rint(v dt / h) (the fixed-point positions; periodic images counted);
+ *   F = -grad U (Eq. 1 and 2) from the rebuilt cell list;
+ *   v += dt/2 F; v *= exp(-xi dt/2); xi += dt/2 (2K - gT)/Q; eta += dt/2 xi,
+ * with K = sum v^2 / 2 per replica (fixed order), g = 3N, Q = g T tau_T^2.
+ * mc_md_setup: dt > 0; tau_T > 0, or <= 0 for no thermostat (constant
+ * energy); T[n_rep] the bath temperatures; v0[3 N] the initial velocities in
+ * site order (host, copied); xi = eta = 0.  The positions are the handle's
+ * state; MD steps and MC sweeps may alternate (after MD steps the running
+ * MC energy restarts from a recompute).
+ * mc_md_run: n_steps steps, each one CUDA graph.  Asynchronous.
+ * mc_md_state: v_out[3 N] (nullable) and per replica out[5 r + {0..4}] =
+ * K, U, xi, eta, and the conserved K + U + Q xi^2/2 + g T eta (K + U without
+ * a thermostat).  Synchronous.
+ * Errors: INVALID_ARG (NULL, dt <= 0, T <= 0, no setup), CUDA.
+ */
+int mc_md_setup(mc_handle *h, double dt, double tau_T, const double *T, const double *v0);
+int mc_md_run(mc_handle *h, int n_steps);
+int mc_md_state(mc_handle *h, double *v_out, double *out);
+
 /* Pick the cell schedule: run n_sweeps sweeps (>= 1) with each schedule (1,
  * 2, 4 and 8 warps per cell, as one persistent launch per call and as one
  * CUDA graph per sweep) from the same state, time them on the handle's stream

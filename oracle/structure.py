@@ -36,9 +36,19 @@ def pair_vectors(L, q, i):
     return d
 
 
+def pair_w(r2, sab, bonded, pot):
+    """-r dphi/dr of pairs at squared distances r2 with mixed diameters sab
+    (arrays), FENE included where bonded."""
+    eps, K, R0 = float(pot[3]), float(pot[4]), float(pot[5])
+    s6 = (sab * sab / r2) ** 3
+    inside = r2 < 2.0 ** (1.0 / 3.0) * sab * sab
+    w = np.where(inside, 24.0 * eps * s6 * (2.0 * s6 - 1.0), 0.0)
+    x = np.where(bonded, r2 / (R0 * sab) ** 2, 0.0)
+    return w + np.where(bonded, -2.0 * K * eps * x / (1.0 - x), 0.0)
+
+
 def virial(L, q, t, pot) -> float:
     sig = np.asarray(pot[:3], dtype=np.float64)
-    eps, K, R0 = float(pot[3]), float(pot[4]), float(pot[5])
     t = np.asarray(t).reshape(-1)
     N = t.size
     W = 0.0
@@ -46,13 +56,8 @@ def virial(L, q, t, pot) -> float:
         d = pair_vectors(L, q, i)
         r2 = (d * d).sum(axis=1)
         sab = 0.5 * (sig[t[i]] + sig[t[i + 1:]])
-        s6 = (sab * sab / r2) ** 3
-        inside = r2 < 2.0 ** (1.0 / 3.0) * sab * sab
-        W += np.where(inside, 24.0 * eps * s6 * (2.0 * s6 - 1.0), 0.0).sum()
         same = (np.arange(i + 1, N) // 3) == (i // 3)
-        if same.any():
-            x = r2[same] / (R0 * sab[same]) ** 2
-            W += (-2.0 * K * eps * x / (1.0 - x)).sum()
+        W += pair_w(r2, sab, same, pot).sum()
     return float(W)
 
 

@@ -11,8 +11,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 SO = os.path.join(OUT_DIR, "libflipmc.so")
-SOURCES = ["cell_list.cu", "sweep.cu", "energy.cu", "engine.cu", "noalloc.cu"]
-HEADERS = ["flipmc_device.cuh", "flipmc_types.h", "cell_list.h", "cell_list_dev.cuh", "energy.h"]
+SOURCES = ["cell_list.cu", "sweep.cu", "energy.cu", "engine.cu", "noalloc.cu", "md.cu"]
+HEADERS = ["flipmc_device.cuh", "flipmc_types.h", "cell_list.h", "cell_list_dev.cuh", "energy.h", "md.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
               "--expt-relaxed-constexpr", "-Xptxas", "-warn-spills"]

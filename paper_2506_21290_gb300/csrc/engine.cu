@@ -21,6 +21,7 @@
 #include "cell_list.h"
 #include "energy.h"
 #include "flipmc_types.h"
+#include "md.h"
 
 using namespace flipmc;
 
@@ -97,6 +98,14 @@ struct mc_handle {
         std::vector<void *> bufs;         // device buffers of the setup
         CorrDev dev{};
     } corr;
+    // molecular dynamics (mc_md_*)
+    struct Md {
+        bool on = false;
+        MdDev dev{};
+        std::vector<double> T, Q;
+        std::vector<void *> bufs;
+        cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    } md;
     std::vector<Buf> allocs;
     // device scratch
     RepInfo *d_rep = nullptr;
@@ -626,12 +635,23 @@ static void corr_free(mc_handle *h)
     h->corr = mc_handle::Corr{};
 }
 
+// Release the buffers and graphs of an MD setup (after the stream is idle).
+static void md_free(mc_handle *h)
+{
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    for (int b = 0; b < 2; ++b)
+        if (h->md.graph[b]) cudaGraphExecDestroy(h->md.graph[b]);
+    for (void *b : h->md.bufs) cudaFree(b);
+    h->md = mc_handle::Md{};
+}
+
 void mc_destroy(mc_handle *h)
 {
     if (!h) return;
     cudaSetDevice(h->device);
     if (h->stream) cudaStreamSynchronize(h->stream);
     corr_free(h);
+    md_free(h);
     for (int b = 0; b < 2; ++b)
         if (h->graph[b]) cudaGraphExecDestroy(h->graph[b]);
     for (auto &a : h->allocs) cudaFree(a.p);
@@ -1401,6 +1421,151 @@ int mc_corr_relaxation_time(mc_handle *h, int which, double level, double *tau)
         }
     }
     return MC_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Molecular dynamics
+// ---------------------------------------------------------------------------
+namespace {
+
+// the cell-list build of an MD step draws no attempt random numbers
+DevState md_state(const mc_handle *h)
+{
+    DevState d = h->ds;
+    d.att_rnd = nullptr;
+    return d;
+}
+
+// One MD step from the records of buf (the cell-sorted current buffer) into buf ^ 1, as a graph.
+int md_graph(mc_handle *h, int buf)
+{
+    if (h->md.graph[buf]) return MC_OK;
+    cudaStream_t cs;
+    CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t g;
+    CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    const DevState d = md_state(h);
+    launch_md_begin(d, h->md.dev, cs);
+    launch_md_drift(d, buf, h->md.dev, cs);
+    launch_cell_list(d, buf, buf ^ 1, cs);
+    launch_md_forces(d, buf ^ 1, h->md.dev, cs);
+    launch_md_end(d, h->md.dev, cs);
+    cudaError_t e = cudaStreamEndCapture(cs, &g);
+    if (e != cudaSuccess) {
+        cudaStreamDestroy(cs);
+        return fail(MC_ERR_CUDA, std::string("MD graph capture: ") + cudaGetErrorString(e));
+    }
+    e = cudaGraphInstantiate(&h->md.graph[buf], g, 0);
+    cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) return fail(MC_ERR_CUDA, std::string("MD graph instantiate: ") + cudaGetErrorString(e));
+    return MC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mc_md_setup(mc_handle *h, double dt, double tau_T, const double *T, const double *v0)
+{
+    if (!h || !T || !v0) return fail(MC_ERR_INVALID_ARG, "NULL argument");
+    if (!(dt > 0.0) || !std::isfinite(dt) || !std::isfinite(tau_T)) return fail(MC_ERR_INVALID_ARG, "dt > 0");
+    for (int r = 0; r < h->n_rep; ++r)
+        if (!(T[r] > 0.0) || !std::isfinite(T[r])) return fail(MC_ERR_INVALID_ARG, "temperature must be positive");
+    int rc = set_device(h);
+    if (rc) return rc;
+    md_free(h);
+    auto &m = h->md;
+    const size_t N = (size_t)h->n_sites;
+    m.T.assign(T, T + h->n_rep);
+    m.Q.resize(h->n_rep);
+    for (int r = 0; r < h->n_rep; ++r)   // tau_T <= 0: no thermostat (Q infinite, xi stays 0)
+        m.Q[r] = tau_T > 0.0 ? 3.0 * h->reps[r].n_sites * T[r] * tau_T * tau_T : HUGE_VAL;
+    double *bufs[7] = {};
+    const size_t sizes[7] = {3 * N, 3 * N, (size_t)h->n_rep, (size_t)h->n_rep, (size_t)h->n_rep, (size_t)h->n_rep,
+                             (size_t)h->n_rep};
+    for (int k = 0; k < 7; ++k) {
+        cudaError_t e = cudaMalloc(&bufs[k], sizeof(double) * sizes[k]);
+        if (e != cudaSuccess) {
+            md_free(h);
+            return fail(MC_ERR_CUDA, std::string("cudaMalloc (MD): ") + cudaGetErrorString(e));
+        }
+        m.bufs.push_back(bufs[k]);
+        CUDA_TRY(cudaMemset(bufs[k], 0, sizeof(double) * sizes[k]));
+    }
+    m.dev.v = bufs[0];
+    m.dev.F = bufs[1];
+    m.dev.xi = bufs[2];
+    m.dev.eta = bufs[3];
+    m.dev.K = bufs[4];
+    m.dev.T = bufs[5];
+    m.dev.Q = bufs[6];
+    m.dev.dt = dt;
+    m.dev.hdt = 0.5 * dt;
+    CUDA_TRY(cudaMemcpy(bufs[0], v0, sizeof(double) * 3 * N, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(bufs[5], m.T.data(), sizeof(double) * h->n_rep, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(bufs[6], m.Q.data(), sizeof(double) * h->n_rep, cudaMemcpyHostToDevice));
+    // the forces of the current state (its cell list is current)
+    launch_md_forces(md_state(h), h->cur, m.dev, h->stream);
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    m.on = true;
+    return check_device_errors(h);
+}
+
+int mc_md_run(mc_handle *h, int n_steps)
+{
+    if (!h) return fail(MC_ERR_INVALID_ARG, "NULL handle");
+    if (!h->md.on) return fail(MC_ERR_INVALID_ARG, "mc_md_setup has not been called");
+    if (n_steps < 0) return fail(MC_ERR_INVALID_ARG, "n_steps < 0");
+    int rc = set_device(h);
+    if (rc) return rc;
+    for (int s = 0; s < n_steps; ++s) {
+        if ((rc = md_graph(h, h->cur))) return rc;
+        CUDA_TRY(cudaGraphLaunch(h->md.graph[h->cur], h->stream));
+        h->cur ^= 1;
+    }
+    // the running energy of later MC sweeps starts from the MD configuration
+    if (n_steps > 0) {
+        if ((rc = enqueue_energy(h))) return rc;
+        CUDA_TRY(cudaMemcpyAsync(h->ds.e_run, h->d_e_out, sizeof(double) * h->n_rep, cudaMemcpyDeviceToDevice,
+                                 h->stream));
+    }
+    CUDA_TRY(cudaGetLastError());
+    return MC_OK;
+}
+
+int mc_md_state(mc_handle *h, double *v_out, double *out)
+{
+    if (!h || !out) return fail(MC_ERR_INVALID_ARG, "NULL argument");
+    if (!h->md.on) return fail(MC_ERR_INVALID_ARG, "mc_md_setup has not been called");
+    int rc = set_device(h);
+    if (rc) return rc;
+    const int R = h->n_rep;
+    std::vector<double> v(3 * (size_t)h->n_sites), xi(R), eta(R), U(R);
+    if ((rc = enqueue_energy(h))) return rc;
+    CUDA_TRY(cudaMemcpyAsync(v.data(), h->md.dev.v, sizeof(double) * v.size(), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaMemcpyAsync(xi.data(), h->md.dev.xi, sizeof(double) * R, cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaMemcpyAsync(eta.data(), h->md.dev.eta, sizeof(double) * R, cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaMemcpyAsync(U.data(), h->d_e_out, sizeof(double) * R, cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    if (v_out) std::memcpy(v_out, v.data(), sizeof(double) * v.size());
+    for (int r = 0; r < R; ++r) {
+        double K = 0.0;
+        const size_t o = 3 * (size_t)h->reps[r].site_off, n = 3 * (size_t)h->reps[r].n_sites;
+        for (size_t k = 0; k < n; ++k) K += 0.5 * v[o + k] * v[o + k];
+        const double g = 3.0 * h->reps[r].n_sites;
+        const double Q = h->md.Q[r];
+        const double thermo = std::isfinite(Q) ? 0.5 * Q * xi[r] * xi[r] + g * h->md.T[r] * eta[r] : 0.0;
+        out[5 * r + 0] = K;
+        out[5 * r + 1] = U[r];
+        out[5 * r + 2] = xi[r];
+        out[5 * r + 3] = eta[r];
+        out[5 * r + 4] = K + U[r] + thermo;
+    }
+    return check_device_errors(h);
 }
 
 int mc_get_info(mc_handle *h, mc_info *info)

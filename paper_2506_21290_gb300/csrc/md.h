@@ -1,0 +1,34 @@
+// Molecular dynamics of the same model (Sec. II.D): velocity Verlet with a
+// Nose-Hoover thermostat, on the fixed-point positions of the MC state.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "flipmc_types.h"
+
+namespace flipmc {
+
+// Device state of an MD run: velocities and forces per site (site order),
+// thermostat variables per replica.
+struct MdDev {
+    double *v;         // 3 per site
+    double *F;         // 3 per site
+    double *xi;        // per replica: thermostat friction
+    double *eta;       // per replica: its time integral (for the conserved energy)
+    double *K;         // per replica: kinetic energy at the last thermostat step
+    const double *T;   // per replica: bath temperature
+    const double *Q;   // per replica: thermostat mass g T tau^2, g = 3 N
+    double dt;
+    double hdt;        // dt / 2
+};
+
+// Thermostat half step, then the scaling and the first half kick (start of a step).
+void launch_md_begin(const DevState &d, const MdDev &m, cudaStream_t st);
+// Positions q += rint(v dt / h) on the records of buf (cell-sorted), periodic images counted.
+void launch_md_drift(const DevState &d, int buf, const MdDev &m, cudaStream_t st);
+// FP64 forces on every atom from its partners in the 27 (or 8) neighbour cells of buf.
+void launch_md_forces(const DevState &d, int buf, const MdDev &m, cudaStream_t st);
+// Second half kick, the scaling, then the thermostat half step (end of a step).
+void launch_md_end(const DevState &d, const MdDev &m, cudaStream_t st);
+
+}  // namespace flipmc

@@ -114,6 +114,9 @@ def load():
         "mc_corr_sums": ([vp, vp], i32),
         "mc_corr_results": ([vp, vp], i32),
         "mc_corr_relaxation_time": ([vp, i32, dbl, vp], i32),
+        "mc_md_setup": ([vp, dbl, dbl, vp, vp], i32),
+        "mc_md_run": ([vp, i32], i32),
+        "mc_md_state": ([vp, vp, vp], i32),
         "mc_last_error": ([], C.c_char_p),
         "mc_energy_noalloc": ([dbl, i32, vp, vp, vp, vp, vp], i32),
     }
@@ -360,6 +363,23 @@ def mc_corr_relaxation_time(h, which, level, n_rep):
     return tau
 
 
+def mc_md_setup(h, dt, tau_T, T, v0):
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    v0 = np.ascontiguousarray(v0, dtype=np.float64).reshape(-1)
+    _check(load().mc_md_setup(h, float(dt), float(tau_T), _ptr(T), _ptr(v0)), "mc_md_setup")
+
+
+def mc_md_run(h, n):
+    _check(load().mc_md_run(h, int(n)), "mc_md_run")
+
+
+def mc_md_state(h, n_sites, n_rep):
+    v = np.zeros((n_sites, 3), dtype=np.float64)
+    out = np.zeros((n_rep, 5), dtype=np.float64)
+    _check(load().mc_md_state(h, _ptr(v), _ptr(out)), "mc_md_state")
+    return v, out
+
+
 def mc_get_info(h):
     i = mc_info()
     _check(load().mc_get_info(h, C.byref(i)), "mc_get_info")
@@ -499,6 +519,17 @@ class Handle:
     def corr_relaxation_time(self, which=0, level=float(np.exp(-1.0))):
         """Per replica: the time at which F_s (0), F_s^cm (1) or C_2 (2) reaches level."""
         return mc_corr_relaxation_time(self.h, which, level, self.n_rep)
+
+    def md_setup(self, dt, tau_T, T, v0):
+        """MD from the current positions: time step dt, thermostat time tau_T (<= 0: none), v0 (N, 3)."""
+        mc_md_setup(self.h, dt, tau_T, np.broadcast_to(np.asarray(T, dtype=np.float64), (self.n_rep,)), v0)
+
+    def md_run(self, n):
+        mc_md_run(self.h, n)
+
+    def md_state(self):
+        """(v (N, 3), per replica [K, U, xi, eta, conserved energy])."""
+        return mc_md_state(self.h, self.N, self.n_rep)
 
     def stats(self):
         return mc_state_stats(self.h, self.n_rep)

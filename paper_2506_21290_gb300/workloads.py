@@ -172,3 +172,10 @@ WORKLOADS = {
     "batched-256": dict(R=256, T=None, seed=0, sweeps=1000, precision="fp32"),
     "large-64000": dict(M=64000, T=T_LOW, seed=3, sweeps=1000, precision="fp32"),
 }
+
+
+def maxwell_velocities(n_sites: int, T: float, seed: int) -> np.ndarray:
+    """Initial MD velocities: each component normal with variance T (m = 1),
+    then the mean velocity removed (seeded, numpy)."""
+    v = np.random.default_rng(seed).normal(scale=math.sqrt(T), size=(n_sites, 3))
+    return v - v.mean(axis=0, keepdims=True)
