@@ -64,6 +64,8 @@ def parse():
                     help="sweeps per schedule for mc_autotune when the schedule is automatic (0: off)")
     ap.add_argument("--one-by-one", type=int, default=16,
                     help="batched workloads: replicas timed one by one on their own handles (0: off)")
+    ap.add_argument("--md", type=int, default=0,
+                    help="also time this many molecular-dynamics steps on the workload (0: off)")
     ap.add_argument("--corr", type=int, default=0,
                     help="also time the multiple-origin correlation sampling with this many origins "
                          "measured per event (0: off)")
@@ -290,6 +292,29 @@ def run_corr(h, wl, mix, P, stream, n_events=10):
                     "for each pair in FP64, fixed-order per-replica sums, one new origin"}
 
 
+def run_md(h, wl, n_steps, stream):
+    """Molecular dynamics on the workload's state after the MC measurement:
+    dt = 0.001, Nose-Hoover with tau = 1 at the workload's temperature(s)."""
+    import torch
+    T = np.broadcast_to(np.asarray(wl["T"], dtype=np.float64), (h.n_rep,))
+    v0 = W.maxwell_velocities(h.N, float(np.mean(T)), 11)
+    h.md_setup(0.001, 1.0, T, v0)
+    h.md_run(20)                      # warm-up, graphs instantiated
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    h.md_run(n_steps)
+    b.record(stream)
+    b.synchronize()
+    ms = a.elapsed_time(b)
+    st = h.md_state()[1]
+    return {"steps": n_steps, "ms_per_step": ms / n_steps, "steps_per_s": n_steps / (ms * 1e-3),
+            "atom_steps_per_s": h.N * n_steps / (ms * 1e-3),
+            "kinetic_temperature": [float(2 * x / (3 * n)) for x, n in zip(st[:, 0], np.full(h.n_rep, h.N // h.n_rep))],
+            "what": "one step: thermostat half + kick, drift, cell-list rebuild (4 kernels), FP64 forces, kick + "
+                    "thermostat half; one CUDA graph per step"}
+
+
 def run_native(args):
     import torch
     from paper_2506_21290_gb300 import build as B
@@ -461,6 +486,8 @@ def run_native(args):
     }
     if args.corr > 0:
         line["corr"] = run_corr(h, wl, mix, args.corr, stream)
+    if args.md > 0:
+        line["md"] = run_md(h, wl, args.md, stream)
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.barrier()

@@ -1483,17 +1483,32 @@ int mc_md_setup(mc_handle *h, double dt, double tau_T, const double *T, const do
     m.Q.resize(h->n_rep);
     for (int r = 0; r < h->n_rep; ++r)   // tau_T <= 0: no thermostat (Q infinite, xi stays 0)
         m.Q[r] = tau_T > 0.0 ? 3.0 * h->reps[r].n_sites * T[r] * tau_T * tau_T : HUGE_VAL;
-    double *bufs[7] = {};
-    const size_t sizes[7] = {3 * N, 3 * N, (size_t)h->n_rep, (size_t)h->n_rep, (size_t)h->n_rep, (size_t)h->n_rep,
-                             (size_t)h->n_rep};
-    for (int k = 0; k < 7; ++k) {
-        cudaError_t e = cudaMalloc(&bufs[k], sizeof(double) * sizes[k]);
+    // chunks of at most kMdChunk atoms, none spanning two replicas
+    std::vector<int> chunk_a0, rep_chunk0;
+    for (int r = 0; r < h->n_rep; ++r) {
+        rep_chunk0.push_back((int)chunk_a0.size());
+        for (int a = 0; a < h->reps[r].n_sites; a += kMdChunk) chunk_a0.push_back(h->reps[r].site_off + a);
+    }
+    const int n_chunks = (int)chunk_a0.size();
+    rep_chunk0.push_back(n_chunks);
+    chunk_a0.push_back((int)N);
+    const size_t R = (size_t)h->n_rep;
+    double *bufs[9] = {};
+    const size_t sizes[9] = {3 * N, 3 * N, R, R, R, R, R, R, (size_t)n_chunks};
+    int *ibufs[2] = {};
+    const size_t isizes[2] = {chunk_a0.size(), rep_chunk0.size()};
+    for (int k = 0; k < 11; ++k) {
+        void *p = nullptr;
+        const size_t bytes = k < 9 ? sizeof(double) * sizes[k] : sizeof(int) * isizes[k - 9];
+        cudaError_t e = cudaMalloc(&p, bytes);
         if (e != cudaSuccess) {
             md_free(h);
             return fail(MC_ERR_CUDA, std::string("cudaMalloc (MD): ") + cudaGetErrorString(e));
         }
-        m.bufs.push_back(bufs[k]);
-        CUDA_TRY(cudaMemset(bufs[k], 0, sizeof(double) * sizes[k]));
+        m.bufs.push_back(p);
+        CUDA_TRY(cudaMemset(p, 0, bytes));
+        if (k < 9) bufs[k] = (double *)p;
+        else ibufs[k - 9] = (int *)p;
     }
     m.dev.v = bufs[0];
     m.dev.F = bufs[1];
@@ -1502,8 +1517,15 @@ int mc_md_setup(mc_handle *h, double dt, double tau_T, const double *T, const do
     m.dev.K = bufs[4];
     m.dev.T = bufs[5];
     m.dev.Q = bufs[6];
+    m.dev.scale = bufs[7];
+    m.dev.part = bufs[8];
+    m.dev.chunk_a0 = ibufs[0];
+    m.dev.rep_chunk0 = ibufs[1];
+    m.dev.n_chunks = n_chunks;
     m.dev.dt = dt;
     m.dev.hdt = 0.5 * dt;
+    CUDA_TRY(cudaMemcpy(ibufs[0], chunk_a0.data(), sizeof(int) * chunk_a0.size(), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(ibufs[1], rep_chunk0.data(), sizeof(int) * rep_chunk0.size(), cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(bufs[0], v0, sizeof(double) * 3 * N, cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(bufs[5], m.T.data(), sizeof(double) * h->n_rep, cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(bufs[6], m.Q.data(), sizeof(double) * h->n_rep, cudaMemcpyHostToDevice));

@@ -147,6 +147,24 @@ __device__ __forceinline__ double virial64(const ModelDev &md, double r2, int ab
     return w;
 }
 
+// The same pair virial divided by r^2 (the force factor: F_i += w (x_i - x_j)),
+// with one FP64 division for the WCA term.
+__device__ __forceinline__ double virial_over_r2(const ModelDev &md, double r2, int ab, bool bonded)
+{
+    const double inv = __ddiv_rn(1.0, r2);
+    double w = 0.0;
+    if (r2 < md.rc2[ab]) {
+        const double t = __dmul_rn(md.s2[ab], inv);
+        const double s6 = __dmul_rn(__dmul_rn(t, t), t);
+        w = __dmul_rn(__dmul_rn(6.0, md.e4), __dmul_rn(s6, __dsub_rn(__dmul_rn(2.0, s6), 1.0)));
+    }
+    if (bonded) {
+        const double x = __ddiv_rn(r2, md.R2[ab]);
+        w = __dadd_rn(w, __dmul_rn(__dmul_rn(2.0, md.nke), __ddiv_rn(x, __dsub_rn(1.0, x))));
+    }
+    return __dmul_rn(w, inv);
+}
+
 // FP32 WCA with its magnitude 4eps s12 + 4eps s6 + eps (the FP32 error scale).
 __device__ __forceinline__ void wca32(const ModelDev &md, float r2, int ab, float &u, float &mag)
 {

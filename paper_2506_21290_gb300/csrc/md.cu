@@ -7,7 +7,8 @@
 //   q  += rint(v dt / h)                     (fixed point, periodic images counted)
 //   cell list; F = forces (Eq. 1 and 2, every pair inside its range)
 //   v += dt/2 F;  v *= exp(-xi dt/2);  xi += dt/2 (2K - gT) / Q;  eta += dt/2 xi
-// K is the kinetic energy sum v^2 / 2 over the replica, in a fixed order.  The
+// K is the kinetic energy sum v^2 / 2 over the replica, in a fixed order
+// (chunks of kMdChunk atoms, then the chunk sums).  The
 // conserved quantity is K + U + Q xi^2 / 2 + g T eta.
 #include "flipmc_device.cuh"
 #include "md.h"
@@ -18,72 +19,61 @@ namespace {
 
 constexpr int MD_BLOCK = 256;
 
-// Fixed-order kinetic energy of replica r: thread k takes atoms k, k + 256, ...
-// in order, then a fixed tree.  Every thread returns the total.
-__device__ double kinetic(const DevState &d, const MdDev &m, int r, double *red)
+}  // namespace
+
+// Partial kinetic energy of one chunk of kMdChunk atoms (one replica's): each
+// thread its atoms in order, then a fixed tree.
+__global__ void __launch_bounds__(MD_BLOCK) md_kin_partial_kernel(MdDev m)
 {
-    const RepInfo ri = d.rep[r];
+    const int a0 = m.chunk_a0[blockIdx.x], a1 = m.chunk_a0[blockIdx.x + 1];
     double s = 0.0;
-    for (int i = threadIdx.x; i < ri.n_sites; i += MD_BLOCK) {
-        const double *v = m.v + 3 * (size_t)(ri.site_off + i);
+    for (int i = a0 + threadIdx.x; i < a1; i += MD_BLOCK) {
+        const double *v = m.v + 3 * (size_t)i;
         s = __dadd_rn(s, __dadd_rn(__dadd_rn(__dmul_rn(v[0], v[0]), __dmul_rn(v[1], v[1])), __dmul_rn(v[2], v[2])));
     }
+    __shared__ double red[MD_BLOCK];
     red[threadIdx.x] = s;
     __syncthreads();
     for (int w = MD_BLOCK / 2; w > 0; w >>= 1) {
         if (threadIdx.x < w) red[threadIdx.x] = __dadd_rn(red[threadIdx.x], red[threadIdx.x + w]);
         __syncthreads();
     }
-    const double K = 0.5 * red[0];
-    __syncthreads();
-    return K;
+    if (threadIdx.x == 0) m.part[blockIdx.x] = red[0];
 }
 
-// xi += dt/2 (2K - gT)/Q, eta += dt/2 xi (thread 0 of the replica's block)
-__device__ void thermostat_half(const DevState &d, const MdDev &m, int r, double K)
+// Per replica (one block): K from the chunk sums (strided, fixed tree), then
+// xi += dt/2 (2K - gT)/Q, eta += dt/2 xi, and the scale exp(-xi dt/2).
+__global__ void __launch_bounds__(128) md_thermo_kernel(DevState d, MdDev m)
 {
+    const int r = blockIdx.x;
+    double s = 0.0;
+    for (int k = m.rep_chunk0[r] + threadIdx.x; k < m.rep_chunk0[r + 1]; k += 128) s = __dadd_rn(s, m.part[k]);
+    __shared__ double red[128];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 64; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] = __dadd_rn(red[threadIdx.x], red[threadIdx.x + w]);
+        __syncthreads();
+    }
+    if (threadIdx.x != 0) return;
+    const double K = 0.5 * red[0];
     const double g = 3.0 * (double)d.rep[r].n_sites;
     const double xi = __dadd_rn(m.xi[r], __dmul_rn(m.hdt, __ddiv_rn(__dsub_rn(2.0 * K, g * m.T[r]), m.Q[r])));
     m.xi[r] = xi;
     m.eta[r] = __dadd_rn(m.eta[r], __dmul_rn(m.hdt, xi));
     m.K[r] = K;
+    m.scale[r] = exp(-xi * m.hdt);
 }
 
-}  // namespace
-
-// One block per replica.
-__global__ void __launch_bounds__(MD_BLOCK) md_begin_kernel(DevState d, MdDev m)
+// Velocity components: BEGIN: v = v s + dt/2 F; END: v = (v + dt/2 F) s.
+template <bool BEGIN>
+__global__ void md_kick_kernel(DevState d, MdDev m)
 {
-    __shared__ double red[MD_BLOCK];
-    __shared__ double scale_s;
-    const int r = blockIdx.x;
-    const double K = kinetic(d, m, r, red);
-    if (threadIdx.x == 0) {
-        thermostat_half(d, m, r, K);
-        scale_s = exp(-m.xi[r] * m.hdt);
-    }
-    __syncthreads();
-    const double sc = scale_s;
-    const RepInfo ri = d.rep[r];
-    for (int k = threadIdx.x; k < 3 * ri.n_sites; k += MD_BLOCK) {
-        const size_t j = 3 * (size_t)ri.site_off + k;
-        m.v[j] = __dadd_rn(__dmul_rn(m.v[j], sc), __dmul_rn(m.hdt, m.F[j]));
-    }
-}
-
-__global__ void __launch_bounds__(MD_BLOCK) md_end_kernel(DevState d, MdDev m)
-{
-    __shared__ double red[MD_BLOCK];
-    const int r = blockIdx.x;
-    const RepInfo ri = d.rep[r];
-    const double sc = exp(-m.xi[r] * m.hdt);
-    for (int k = threadIdx.x; k < 3 * ri.n_sites; k += MD_BLOCK) {
-        const size_t j = 3 * (size_t)ri.site_off + k;
-        m.v[j] = __dmul_rn(__dadd_rn(m.v[j], __dmul_rn(m.hdt, m.F[j])), sc);
-    }
-    __syncthreads();
-    const double K = kinetic(d, m, r, red);
-    if (threadIdx.x == 0) thermostat_half(d, m, r, K);
+    const size_t j = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= 3 * (size_t)d.n_sites) return;
+    const double sc = m.scale[d.rep_of_site[j / 3]];
+    m.v[j] = BEGIN ? __dadd_rn(__dmul_rn(m.v[j], sc), __dmul_rn(m.hdt, m.F[j]))
+                   : __dmul_rn(__dadd_rn(m.v[j], __dmul_rn(m.hdt, m.F[j])), sc);
 }
 
 __global__ void md_drift_kernel(DevState d, int buf, MdDev m)
@@ -152,7 +142,7 @@ __global__ void md_force_kernel(DevState d, int buf, MdDev m)
                 if (ex * ex + ey * ey + ez * ez > pre) continue;
             }
             const double r2 = r2_fixed64(dx, dy, dz, ri.h);
-            const double w = __ddiv_rn(virial64(md, r2, 3 * ti + rec_type(o.w), bonded), r2);
+            const double w = virial_over_r2(md, r2, 3 * ti + rec_type(o.w), bonded);
             fx = __dsub_rn(fx, __dmul_rn(w, __dmul_rn((double)dx, ri.h)));
             fy = __dsub_rn(fy, __dmul_rn(w, __dmul_rn((double)dy, ri.h)));
             fz = __dsub_rn(fz, __dmul_rn(w, __dmul_rn((double)dz, ri.h)));
@@ -166,7 +156,9 @@ __global__ void md_force_kernel(DevState d, int buf, MdDev m)
 
 void launch_md_begin(const DevState &d, const MdDev &m, cudaStream_t st)
 {
-    md_begin_kernel<<<d.n_rep, MD_BLOCK, 0, st>>>(d, m);
+    md_kin_partial_kernel<<<m.n_chunks, MD_BLOCK, 0, st>>>(m);
+    md_thermo_kernel<<<d.n_rep, 128, 0, st>>>(d, m);
+    md_kick_kernel<true><<<(unsigned)((3 * (size_t)d.n_sites + 255) / 256), 256, 0, st>>>(d, m);
 }
 
 void launch_md_drift(const DevState &d, int buf, const MdDev &m, cudaStream_t st)
@@ -181,7 +173,10 @@ void launch_md_forces(const DevState &d, int buf, const MdDev &m, cudaStream_t s
 
 void launch_md_end(const DevState &d, const MdDev &m, cudaStream_t st)
 {
-    md_end_kernel<<<d.n_rep, MD_BLOCK, 0, st>>>(d, m);
+    md_kick_kernel<false><<<(unsigned)((3 * (size_t)d.n_sites + 255) / 256), 256, 0, st>>>(d, m);
+    md_kin_partial_kernel<<<m.n_chunks, MD_BLOCK, 0, st>>>(m);
+    md_thermo_kernel<<<d.n_rep, 128, 0, st>>>(d, m);
 }
+
 
 }  // namespace flipmc

@@ -18,9 +18,16 @@ struct MdDev {
     double *K;         // per replica: kinetic energy at the last thermostat step
     const double *T;   // per replica: bath temperature
     const double *Q;   // per replica: thermostat mass g T tau^2, g = 3 N
+    double *scale;     // per replica: exp(-xi dt/2) of the current xi
+    double *part;      // per chunk: partial kinetic energy
+    const int *chunk_a0;     // per chunk: first atom (global); [n_chunks] = all atoms
+    const int *rep_chunk0;   // per replica: first chunk; [n_rep] = n_chunks
+    int n_chunks;
     double dt;
     double hdt;        // dt / 2
 };
+
+constexpr int kMdChunk = 2048;   // atoms per block of the kinetic-energy partial sums
 
 // Thermostat half step, then the scaling and the first half kick (start of a step).
 void launch_md_begin(const DevState &d, const MdDev &m, cudaStream_t st);
