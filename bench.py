@@ -294,25 +294,26 @@ def run_corr(h, wl, mix, P, stream, n_events=10):
 
 def run_md(h, wl, n_steps, stream):
     """Molecular dynamics on the workload's state after the MC measurement:
-    dt = 0.001, Nose-Hoover with tau = 1 at the workload's temperature(s)."""
+    dt = 0.001, Nose-Hoover with tau = 1 at the workload's temperature(s),
+    with FP64 and with FP32 pair forces."""
     import torch
     T = np.broadcast_to(np.asarray(wl["T"], dtype=np.float64), (h.n_rep,))
-    v0 = W.maxwell_velocities(h.N, float(np.mean(T)), 11)
-    h.md_setup(0.001, 1.0, T, v0)
-    h.md_run(20)                      # warm-up, graphs instantiated
-    a = torch.cuda.Event(enable_timing=True)
-    b = torch.cuda.Event(enable_timing=True)
-    a.record(stream)
-    h.md_run(n_steps)
-    b.record(stream)
-    b.synchronize()
-    ms = a.elapsed_time(b)
-    st = h.md_state()[1]
-    return {"steps": n_steps, "ms_per_step": ms / n_steps, "steps_per_s": n_steps / (ms * 1e-3),
-            "atom_steps_per_s": h.N * n_steps / (ms * 1e-3),
-            "kinetic_temperature": [float(2 * x / (3 * n)) for x, n in zip(st[:, 0], np.full(h.n_rep, h.N // h.n_rep))],
-            "what": "one step: thermostat half + kick, drift, cell-list rebuild (4 kernels), FP64 forces, kick + "
-                    "thermostat half; one CUDA graph per step"}
+    out = {"steps": n_steps,
+           "what": "one step: thermostat half + kick, drift, cell-list rebuild (4 kernels), forces, kick + "
+                   "thermostat half; one CUDA graph per step"}
+    for prec in ("fp64", "fp32"):
+        h.md_setup(0.001, 1.0, T, W.maxwell_velocities(h.N, float(np.mean(T)), 11), force_precision=prec)
+        h.md_run(20)                      # warm-up, graphs instantiated
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        h.md_run(n_steps)
+        b.record(stream)
+        b.synchronize()
+        ms = a.elapsed_time(b)
+        out[prec + "_forces"] = {"ms_per_step": ms / n_steps, "steps_per_s": n_steps / (ms * 1e-3),
+                                 "atom_steps_per_s": h.N * n_steps / (ms * 1e-3)}
+    return out
 
 
 def run_native(args):

@@ -408,14 +408,17 @@ int mc_corr_relaxation_time(mc_handle *h, int which, double level, double *tau);
  * energy); T[n_rep] the bath temperatures; v0[3 N] the initial velocities in
  * site order (host, copied); xi = eta = 0.  The positions are the handle's
  * state; MD steps and MC sweeps may alternate (after MD steps the running
- * MC energy restarts from a recompute).
+ * MC energy restarts from a recompute).  force_precision: MC_PREC_FP64 (pair
+ * forces in FP64, the oracle-parity path) or MC_PREC_FP32 (pair terms and
+ * their per-atom sums in FP32, from the exact int32 differences; velocities,
+ * positions, the thermostat and energies stay FP64).
  * mc_md_run: n_steps steps, each one CUDA graph.  Asynchronous.
  * mc_md_state: v_out[3 N] (nullable) and per replica out[5 r + {0..4}] =
  * K, U, xi, eta, and the conserved K + U + Q xi^2/2 + g T eta (K + U without
  * a thermostat).  Synchronous.
  * Errors: INVALID_ARG (NULL, dt <= 0, T <= 0, no setup), CUDA.
  */
-int mc_md_setup(mc_handle *h, double dt, double tau_T, const double *T, const double *v0);
+int mc_md_setup(mc_handle *h, double dt, double tau_T, const double *T, const double *v0, int force_precision);
 int mc_md_run(mc_handle *h, int n_steps);
 int mc_md_state(mc_handle *h, double *v_out, double *out);
 

@@ -1468,8 +1468,10 @@ int md_graph(mc_handle *h, int buf)
 
 extern "C" {
 
-int mc_md_setup(mc_handle *h, double dt, double tau_T, const double *T, const double *v0)
+int mc_md_setup(mc_handle *h, double dt, double tau_T, const double *T, const double *v0, int force_precision)
 {
+    if (force_precision != MC_PREC_FP64 && force_precision != MC_PREC_FP32)
+        return fail(MC_ERR_INVALID_ARG, "force_precision: MC_PREC_FP64 or MC_PREC_FP32");
     if (!h || !T || !v0) return fail(MC_ERR_INVALID_ARG, "NULL argument");
     if (!(dt > 0.0) || !std::isfinite(dt) || !std::isfinite(tau_T)) return fail(MC_ERR_INVALID_ARG, "dt > 0");
     for (int r = 0; r < h->n_rep; ++r)
@@ -1522,6 +1524,7 @@ int mc_md_setup(mc_handle *h, double dt, double tau_T, const double *T, const do
     m.dev.chunk_a0 = ibufs[0];
     m.dev.rep_chunk0 = ibufs[1];
     m.dev.n_chunks = n_chunks;
+    m.dev.fp32_forces = force_precision == MC_PREC_FP32 ? 1 : 0;
     m.dev.dt = dt;
     m.dev.hdt = 0.5 * dt;
     CUDA_TRY(cudaMemcpy(ibufs[0], chunk_a0.data(), sizeof(int) * chunk_a0.size(), cudaMemcpyHostToDevice));

@@ -99,8 +99,28 @@ __global__ void md_drift_kernel(DevState d, int buf, MdDev m)
     d.rec[buf][g] = rc;
 }
 
+// The pair factor (-r dphi/dr) / r^2 in FP32: r^2 from the exact int32
+// differences (one rounding per axis), the derivative of Eq. 1 and Eq. 2.
+__device__ __forceinline__ float virial_over_r2_f32(const ModelDev &md, float r2, int ab, bool bonded)
+{
+    const float inv = 1.0f / r2;
+    float w = 0.f;
+    if (r2 < md.rc2f[ab]) {
+        const float t = md.s2f[ab] * inv;
+        const float s6 = t * t * t;
+        w = 6.0f * md.e4f * s6 * (2.0f * s6 - 1.0f);
+    }
+    if (bonded) {
+        const float x = r2 * md.invR2f[ab];
+        w += 2.0f * md.nkef * x / (1.0f - x);
+    }
+    return w * inv;
+}
+
 // F_i = sum over partners j of (-r dphi/dr) / r^2 (x_i - x_j), partners in
-// the neighbour cells in cell order, then record order.
+// the neighbour cells in cell order, then record order; FP64, or FP32 terms
+// summed in FP32 (FP32 = true).
+template <bool FP32>
 __global__ void md_force_kernel(DevState d, int buf, MdDev m)
 {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
@@ -121,6 +141,7 @@ __global__ void md_force_kernel(DevState d, int buf, MdDev m)
     const bool small = nc == 2;
     const int ns = small ? 8 : 27;
     double fx = 0.0, fy = 0.0, fz = 0.0;
+    float gx = 0.f, gy = 0.f, gz = 0.f;
     for (int k = 0; k < ns; ++k) {
         int ox, oy, oz;
         if (small) {
@@ -141,17 +162,26 @@ __global__ void md_force_kernel(DevState d, int buf, MdDev m)
                 const float ex = (float)dx * ri.hf, ey = (float)dy * ri.hf, ez = (float)dz * ri.hf;
                 if (ex * ex + ey * ey + ez * ez > pre) continue;
             }
-            const double r2 = r2_fixed64(dx, dy, dz, ri.h);
-            const double w = virial_over_r2(md, r2, 3 * ti + rec_type(o.w), bonded);
-            fx = __dsub_rn(fx, __dmul_rn(w, __dmul_rn((double)dx, ri.h)));
-            fy = __dsub_rn(fy, __dmul_rn(w, __dmul_rn((double)dy, ri.h)));
-            fz = __dsub_rn(fz, __dmul_rn(w, __dmul_rn((double)dz, ri.h)));
+            if (FP32) {
+                const float ex = (float)dx * ri.hf, ey = (float)dy * ri.hf, ez = (float)dz * ri.hf;
+                const float w = virial_over_r2_f32(md, fmaf(ex, ex, fmaf(ey, ey, ez * ez)), 3 * ti + rec_type(o.w),
+                                                   bonded);
+                gx = fmaf(-w, ex, gx);
+                gy = fmaf(-w, ey, gy);
+                gz = fmaf(-w, ez, gz);
+            } else {
+                const double r2 = r2_fixed64(dx, dy, dz, ri.h);
+                const double w = virial_over_r2(md, r2, 3 * ti + rec_type(o.w), bonded);
+                fx = __dsub_rn(fx, __dmul_rn(w, __dmul_rn((double)dx, ri.h)));
+                fy = __dsub_rn(fy, __dmul_rn(w, __dmul_rn((double)dy, ri.h)));
+                fz = __dsub_rn(fz, __dmul_rn(w, __dmul_rn((double)dz, ri.h)));
+            }
         }
     }
     double *F = m.F + 3 * (size_t)(ri.site_off + si);
-    F[0] = fx;
-    F[1] = fy;
-    F[2] = fz;
+    F[0] = FP32 ? (double)gx : fx;
+    F[1] = FP32 ? (double)gy : fy;
+    F[2] = FP32 ? (double)gz : fz;
 }
 
 void launch_md_begin(const DevState &d, const MdDev &m, cudaStream_t st)
@@ -168,7 +198,8 @@ void launch_md_drift(const DevState &d, int buf, const MdDev &m, cudaStream_t st
 
 void launch_md_forces(const DevState &d, int buf, const MdDev &m, cudaStream_t st)
 {
-    md_force_kernel<<<(d.n_sites + 255) / 256, 256, 0, st>>>(d, buf, m);
+    if (m.fp32_forces) md_force_kernel<true><<<(d.n_sites + 255) / 256, 256, 0, st>>>(d, buf, m);
+    else md_force_kernel<false><<<(d.n_sites + 255) / 256, 256, 0, st>>>(d, buf, m);
 }
 
 void launch_md_end(const DevState &d, const MdDev &m, cudaStream_t st)

@@ -23,6 +23,7 @@ struct MdDev {
     const int *chunk_a0;     // per chunk: first atom (global); [n_chunks] = all atoms
     const int *rep_chunk0;   // per replica: first chunk; [n_rep] = n_chunks
     int n_chunks;
+    int fp32_forces;   // 1: pair forces in FP32 (velocities, positions and thermostat stay FP64)
     double dt;
     double hdt;        // dt / 2
 };
@@ -33,7 +34,7 @@ constexpr int kMdChunk = 2048;   // atoms per block of the kinetic-energy partia
 void launch_md_begin(const DevState &d, const MdDev &m, cudaStream_t st);
 // Positions q += rint(v dt / h) on the records of buf (cell-sorted), periodic images counted.
 void launch_md_drift(const DevState &d, int buf, const MdDev &m, cudaStream_t st);
-// FP64 forces on every atom from its partners in the 27 (or 8) neighbour cells of buf.
+// Forces on every atom from its partners in the 27 (or 8) neighbour cells of buf (FP64, or FP32 pair terms).
 void launch_md_forces(const DevState &d, int buf, const MdDev &m, cudaStream_t st);
 // Second half kick, the scaling, then the thermostat half step (end of a step).
 void launch_md_end(const DevState &d, const MdDev &m, cudaStream_t st);

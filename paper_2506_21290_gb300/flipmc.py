@@ -114,7 +114,7 @@ def load():
         "mc_corr_sums": ([vp, vp], i32),
         "mc_corr_results": ([vp, vp], i32),
         "mc_corr_relaxation_time": ([vp, i32, dbl, vp], i32),
-        "mc_md_setup": ([vp, dbl, dbl, vp, vp], i32),
+        "mc_md_setup": ([vp, dbl, dbl, vp, vp, i32], i32),
         "mc_md_run": ([vp, i32], i32),
         "mc_md_state": ([vp, vp, vp], i32),
         "mc_last_error": ([], C.c_char_p),
@@ -363,10 +363,11 @@ def mc_corr_relaxation_time(h, which, level, n_rep):
     return tau
 
 
-def mc_md_setup(h, dt, tau_T, T, v0):
+def mc_md_setup(h, dt, tau_T, T, v0, force_precision="fp64"):
     T = np.ascontiguousarray(T, dtype=np.float64)
     v0 = np.ascontiguousarray(v0, dtype=np.float64).reshape(-1)
-    _check(load().mc_md_setup(h, float(dt), float(tau_T), _ptr(T), _ptr(v0)), "mc_md_setup")
+    fp = MC_PREC_FP32 if force_precision == "fp32" else MC_PREC_FP64
+    _check(load().mc_md_setup(h, float(dt), float(tau_T), _ptr(T), _ptr(v0), fp), "mc_md_setup")
 
 
 def mc_md_run(h, n):
@@ -520,9 +521,11 @@ class Handle:
         """Per replica: the time at which F_s (0), F_s^cm (1) or C_2 (2) reaches level."""
         return mc_corr_relaxation_time(self.h, which, level, self.n_rep)
 
-    def md_setup(self, dt, tau_T, T, v0):
-        """MD from the current positions: time step dt, thermostat time tau_T (<= 0: none), v0 (N, 3)."""
-        mc_md_setup(self.h, dt, tau_T, np.broadcast_to(np.asarray(T, dtype=np.float64), (self.n_rep,)), v0)
+    def md_setup(self, dt, tau_T, T, v0, force_precision="fp64"):
+        """MD from the current positions: time step dt, thermostat time tau_T (<= 0: none), v0 (N, 3),
+        pair forces in "fp64" or "fp32"."""
+        mc_md_setup(self.h, dt, tau_T, np.broadcast_to(np.asarray(T, dtype=np.float64), (self.n_rep,)), v0,
+                    force_precision)
 
     def md_run(self, n):
         mc_md_run(self.h, n)
