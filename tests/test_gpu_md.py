@@ -125,3 +125,30 @@ def test_fp32_forces_follow_the_fp64_trajectory():
     print("FP32 forces: max |dv| %.2e, max |dx| %.2e, energy drift %.2e over 2000 steps"
           % (np.max(np.abs(va - vb)), np.max(np.abs(Xa - Xb)) * h, (E1 - E0) / abs(E0)))
     assert abs(E1 - E0) < 1e-3 * abs(E0)
+
+
+def test_md_of_a_batch_equals_each_replica_alone():
+    """Replicas of different size and temperature advanced together give, bit
+    for bit, what each gives on its own handle: the kinetic-energy chunks and
+    the forces are per replica."""
+    Ms, Ts = [64, 125], [1.2, 2.0]
+    Ls = [W.box_length(m) for m in Ms]
+    st = [W.lattice_start(m, l, 20 + k) for k, (m, l) in enumerate(zip(Ms, Ls))]
+    v0 = [W.maxwell_velocities(3 * m, T, 30 + k) for k, (m, T) in enumerate(zip(Ms, Ts))]
+    hb = F.Handle(np.array(Ls), np.concatenate([s[0] for s in st]), np.concatenate([s[1] for s in st]), POT,
+                  precision="fp32", n_mol=np.array(Ms))
+    hb.md_setup(0.001, 1.0, np.array(Ts), np.concatenate(v0), force_precision="fp32")
+    hb.md_run(150)
+    vb, sb = hb.md_state()
+    qb, Xb, tb = hb.state_fixed()
+    off = 0
+    for k, M in enumerate(Ms):
+        h = F.Handle(Ls[k], st[k][0], st[k][1], POT, precision="fp32")
+        h.md_setup(0.001, 1.0, Ts[k], v0[k], force_precision="fp32")
+        h.md_run(150)
+        v, s1 = h.md_state()
+        q, X, t = h.state_fixed()
+        sl = slice(off, off + 3 * M)
+        assert np.array_equal(vb[sl], v) and np.array_equal(Xb[sl], X), k
+        assert sb[k, 2] == s1[0, 2]                                    # xi
+        off += 3 * M
