@@ -46,3 +46,34 @@ def test_create_fails_loudly_without_a_gpu(lib):
         F.Handle(5.0, xyz, t, W.PAPER_POT)
     assert e.value.code in (F.MC_ERR_NO_DEVICE, F.MC_ERR_CUDA)
     assert F.mc_last_error()
+
+
+def test_header_is_plain_c_and_cpp(tmp_path):
+    import shutil
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no gcc")
+    for lang, std in (("c", "-std=c99"), ("c++", "-std=c++17")):
+        r = subprocess.run([gcc, "-fsyntax-only", "-Wall", "-Werror", std, "-x", lang, F.HEADER],
+                           capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
+
+
+def test_c_program_links_every_entry_point(lib, tmp_path):
+    """A C program that takes the address of every declared function links
+    against the library (no call runs: this host has no GPU)."""
+    import os
+    import shutil
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no gcc")
+    names = F.header_symbols()
+    src = tmp_path / "use.c"
+    src.write_text('#include "%s"\n#include <stdio.h>\nint main(void) {\n    void *p[] = {%s};\n'
+                   '    printf("%%d\\n", (int)(sizeof p / sizeof p[0]));\n    return p[0] == 0;\n}\n'
+                   % (F.HEADER, ", ".join("(void *)%s" % n for n in names)))
+    exe = tmp_path / "use"
+    libdir = os.path.dirname(B.SO)
+    r = subprocess.run([gcc, "-std=c99", str(src), "-o", str(exe), "-L" + libdir, "-lflipmc",
+                        "-Wl,-rpath," + libdir], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
