@@ -921,8 +921,12 @@ int mc_structure_factor(mc_handle *h, const double *qvec, int n_q, double *out)
     if (rc) return rc;
     double *dq = nullptr, *dout = nullptr;
     CUDA_TRY(cudaMallocAsync(&dq, sizeof(double) * 3 * n_q, h->stream));
-    CUDA_TRY(cudaMallocAsync(&dout, sizeof(double) * (size_t)n_q * h->n_rep, h->stream));
-    cudaError_t e = cudaMemcpyAsync(dq, qvec, sizeof(double) * 3 * n_q, cudaMemcpyHostToDevice, h->stream);
+    cudaError_t e = cudaMallocAsync(&dout, sizeof(double) * (size_t)n_q * h->n_rep, h->stream);
+    if (e != cudaSuccess) {
+        cudaFreeAsync(dq, h->stream);
+        return fail(MC_ERR_CUDA, std::string("structure factor: ") + cudaGetErrorString(e));
+    }
+    e = cudaMemcpyAsync(dq, qvec, sizeof(double) * 3 * n_q, cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) {
         launch_gather(h->ds, h->cur, h->d_X, h->d_types, h->stream);
         launch_sq(h->ds, h->d_X, dq, n_q, dout, h->stream);
