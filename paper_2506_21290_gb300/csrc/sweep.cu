@@ -1,6 +1,6 @@
 // Checkerboard Metropolis sweep (arXiv 2506.21290 Sec. II.B on a cell grid).
 //
-// A group of W warps (W = 1, 2 or 4) owns one active cell of the current
+// A group of W warps (W = 1, 2, 4 or 8) owns one active cell of the current
 // colour.  It stages the raw records of the cell and of its neighbour cells
 // (27, or the 8 distinct cells when n_c = 2) in shared memory, one bulk copy
 // per cell, and loads the draws of its attempts, which the cell-list build
