@@ -349,6 +349,15 @@ int mc_corr_setup(mc_handle *h, int n_lags, const int64_t *lags, int origin_ever
                   const double *qvec_atom, int n_qa, const double *qvec_cm, int n_qc);
 
 /*
+ * The origin schedule of mc_corr_setup / mc_corr_run, replayed on the host
+ * alone (no handle, no GPU): counts[n_lags] = the number of samples each lag
+ * holds after n_sweeps sweeps (n_sweeps >= 0).  Same rules for the arguments
+ * as mc_corr_setup.  Errors: INVALID_ARG.
+ */
+int mc_corr_schedule(int n_lags, const int64_t *lags, int origin_every, int max_origins, int64_t n_sweeps,
+                     int64_t *counts);
+
+/*
  * n_sweeps sweeps (as mc_sweep_batch: the chain is the one that call would
  * make) with the correlation events of each time on the way.  Sweeps between
  * two event times run as one launch.  Asynchronous like mc_sweep_batch.

@@ -1190,12 +1190,43 @@ ObsState corr_slot(const mc_handle *h, int s)
     return o;
 }
 
-// The events of the current time t: samples of the live origins whose lag
-// has come, retirement of origins past the last lag, a new origin.
+// The decisions of the events at time t (host bookkeeping only): the live
+// origins whose lag has come (slot, lag index), in slot order; then origins
+// with t - t_o >= the last lag retire; then, at a multiple of every, the first
+// free slot takes a new origin (new_slot, or -1).
+struct CorrDecision {
+    std::vector<std::pair<int, int>> pairs;
+    int new_slot = -1;
+};
+
+CorrDecision corr_decide(std::vector<long long> &slot_t0, const std::vector<long long> &lags, int every, long long t)
+{
+    CorrDecision dd;
+    const int n_slots = (int)slot_t0.size();
+    for (int s = 0; s < n_slots; ++s) {
+        if (slot_t0[s] < 0) continue;
+        const auto it = std::lower_bound(lags.begin(), lags.end(), t - slot_t0[s]);
+        if (it != lags.end() && *it == t - slot_t0[s]) dd.pairs.emplace_back(s, (int)(it - lags.begin()));
+    }
+    for (int s = 0; s < n_slots; ++s)
+        if (slot_t0[s] >= 0 && t - slot_t0[s] >= lags.back()) slot_t0[s] = -1;
+    if (t % every == 0) {
+        int s = 0;
+        while (s < n_slots && slot_t0[s] >= 0) ++s;
+        if (s < n_slots) {
+            slot_t0[s] = t;
+            dd.new_slot = s;
+        }
+    }
+    return dd;
+}
+
+// The events of the current time t: the samples (launched before any slot is
+// reused), then the new origin and its lag-0 sample.
 int corr_events(mc_handle *h)
 {
     auto &c = h->corr;
-    const long long t = c.t;
+    const CorrDecision dd = corr_decide(c.slot_t0, c.lags, c.every, c.t);
     bool gathered = false;
     CorrPairs p{};
     auto gather = [&]() {
@@ -1209,31 +1240,20 @@ int corr_events(mc_handle *h)
         }
         p.n = 0;
     };
-    const int n_slots = (int)c.slot_t0.size();
-    for (int s = 0; s < n_slots; ++s) {
-        if (c.slot_t0[s] < 0) continue;
-        const auto it = std::lower_bound(c.lags.begin(), c.lags.end(), t - c.slot_t0[s]);
-        if (it == c.lags.end() || *it != t - c.slot_t0[s]) continue;
-        p.slot[p.n] = s;
-        p.lag[p.n] = (int)(it - c.lags.begin());
+    for (const auto &sl : dd.pairs) {
+        p.slot[p.n] = sl.first;
+        p.lag[p.n] = sl.second;
         if (++p.n == kCorrMaxPairs) flush();
     }
     flush();
-    for (int s = 0; s < n_slots; ++s)
-        if (c.slot_t0[s] >= 0 && t - c.slot_t0[s] >= c.lags.back()) c.slot_t0[s] = -1;
-    if (t % c.every == 0) {
-        int s = 0;
-        while (s < n_slots && c.slot_t0[s] >= 0) ++s;
-        if (s < n_slots) {
-            gather();
-            launch_set_t0(h->ds, h->d_X, h->d_types, corr_slot(h, s), h->stream);
-            c.slot_t0[s] = t;
-            if (c.lags[0] == 0) {
-                p.slot[0] = s;
-                p.lag[0] = 0;
-                p.n = 1;
-                flush();
-            }
+    if (dd.new_slot >= 0) {
+        gather();
+        launch_set_t0(h->ds, h->d_X, h->d_types, corr_slot(h, dd.new_slot), h->stream);
+        if (c.lags[0] == 0) {
+            p.slot[0] = dd.new_slot;
+            p.lag[0] = 0;
+            p.n = 1;
+            flush();
         }
     }
     CUDA_TRY(cudaGetLastError());
@@ -1257,18 +1277,61 @@ long long corr_next(const mc_handle::Corr &c)
 
 extern "C" {
 
-int mc_corr_setup(mc_handle *h, int n_lags, const int64_t *lags, int origin_every, int max_origins,
-                  const double *qvec_atom, int n_qa, const double *qvec_cm, int n_qc)
+}  // extern "C"
+
+namespace {
+
+int corr_validate(int n_lags, const int64_t *lags, int origin_every, int max_origins)
 {
-    if (!h || !lags || !qvec_atom || !qvec_cm) return fail(MC_ERR_INVALID_ARG, "NULL argument");
+    if (!lags) return fail(MC_ERR_INVALID_ARG, "NULL lags");
     if (n_lags < 1 || n_lags > 1024) return fail(MC_ERR_INVALID_ARG, "1 <= n_lags <= 1024");
     for (int l = 0; l < n_lags; ++l)
         if (lags[l] < 0 || (l > 0 && lags[l] <= lags[l - 1]))
             return fail(MC_ERR_INVALID_ARG, "lags must be strictly increasing and >= 0");
     if (origin_every < 1) return fail(MC_ERR_INVALID_ARG, "origin_every >= 1");
     if (max_origins < 1 || max_origins > 1024) return fail(MC_ERR_INVALID_ARG, "1 <= max_origins <= 1024");
+    return MC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mc_corr_schedule(int n_lags, const int64_t *lags, int origin_every, int max_origins, int64_t n_sweeps,
+                     int64_t *counts)
+{
+    int rc = corr_validate(n_lags, lags, origin_every, max_origins);
+    if (rc) return rc;
+    if (!counts || n_sweeps < 0) return fail(MC_ERR_INVALID_ARG, "NULL counts or n_sweeps < 0");
+    mc_handle::Corr c;
+    c.lags.assign(lags, lags + n_lags);
+    c.every = origin_every;
+    c.slot_t0.assign(max_origins, -1);
+    for (int l = 0; l < n_lags; ++l) counts[l] = 0;
+    auto tally = [&]() {
+        const CorrDecision dd = corr_decide(c.slot_t0, c.lags, c.every, c.t);
+        for (const auto &sl : dd.pairs) counts[sl.second] += 1;
+        if (dd.new_slot >= 0 && c.lags[0] == 0) counts[0] += 1;
+    };
+    c.t = 0;
+    tally();
+    while (true) {
+        const long long nxt = corr_next(c);
+        if (nxt > n_sweeps) break;
+        c.t = nxt;
+        tally();
+    }
+    return MC_OK;
+}
+
+int mc_corr_setup(mc_handle *h, int n_lags, const int64_t *lags, int origin_every, int max_origins,
+                  const double *qvec_atom, int n_qa, const double *qvec_cm, int n_qc)
+{
+    if (!h || !lags || !qvec_atom || !qvec_cm) return fail(MC_ERR_INVALID_ARG, "NULL argument");
+    int rc = corr_validate(n_lags, lags, origin_every, max_origins);
+    if (rc) return rc;
     if (n_qa < 1 || n_qa > 256 || n_qc < 1 || n_qc > 256) return fail(MC_ERR_INVALID_ARG, "1 <= n_q <= 256");
-    int rc = set_device(h);
+    rc = set_device(h);
     if (rc) return rc;
     corr_free(h);
     auto &c = h->corr;

@@ -110,6 +110,7 @@ def load():
         "mc_structure_factor": ([vp, vp, i32, vp], i32),
         "mc_pair_histogram": ([vp, dbl, i32, vp, vp], i32),
         "mc_corr_setup": ([vp, i32, vp, i32, i32, vp, i32, vp, i32], i32),
+        "mc_corr_schedule": ([i32, vp, i32, i32, C.c_int64, vp], i32),
         "mc_corr_run": ([vp, i32, vp, vp, vp], i32),
         "mc_corr_sums": ([vp, vp], i32),
         "mc_corr_results": ([vp, vp], i32),
@@ -336,6 +337,15 @@ def mc_corr_setup(h, lags, origin_every, max_origins, qa, qc):
     qc = np.ascontiguousarray(qc, dtype=np.float64).reshape(-1, 3)
     _check(load().mc_corr_setup(h, len(lags), _ptr(lags), int(origin_every), int(max_origins), _ptr(qa), len(qa),
                                 _ptr(qc), len(qc)), "mc_corr_setup")
+
+
+def mc_corr_schedule(lags, origin_every, max_origins, n_sweeps):
+    """Samples per lag after n_sweeps sweeps of mc_corr_run (host only)."""
+    lags = np.ascontiguousarray(lags, dtype=np.int64).reshape(-1)
+    counts = np.zeros(len(lags), dtype=np.int64)
+    _check(load().mc_corr_schedule(len(lags), _ptr(lags), int(origin_every), int(max_origins), int(n_sweeps),
+                                   _ptr(counts)), "mc_corr_schedule")
+    return counts
 
 
 def mc_corr_run(h, n, T, mix, seeds):
