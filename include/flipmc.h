@@ -394,6 +394,14 @@ int mc_corr_sums(mc_handle *h, double *sums);
 int mc_corr_results(mc_handle *h, double *out);
 
 /*
+ * The derivation of mc_corr_results on its own (host only, no handle): n_rows
+ * rows of MC_CORR_NSUM sums (layout of mc_corr_sums) into rows of
+ * MC_CORR_NRES results, n_atoms[k] the atoms N of row k's replica (a positive
+ * multiple of 3).  Errors: INVALID_ARG.
+ */
+int mc_corr_derive(int n_rows, const double *sums, const int32_t *n_atoms, double *out);
+
+/*
  * Relaxation time per replica (Sec. III.C: the time at which a correlation
  * function reaches e^-1): the first lag l (in increasing order, lags with no
  * sample skipped) at which the average of which = 0 (F_s), 1 (F_s^cm) or
@@ -403,6 +411,14 @@ int mc_corr_results(mc_handle *h, double *out);
  * Synchronous.  Errors: INVALID_ARG (no setup, which out of range).
  */
 int mc_corr_relaxation_time(mc_handle *h, int which, double level, double *tau);
+
+/*
+ * The same interpolation on one series (host only): values[l] at lags[l]
+ * (increasing), counts[l] > 0 where the lag has samples; *tau as above.
+ * Errors: INVALID_ARG.
+ */
+int mc_relaxation_time(int n_lags, const int64_t *lags, const double *values, const double *counts, double level,
+                       double *tau);
 
 /*
  * Molecular dynamics of the same model (Sec. II.D: NVT, time step 0.001,

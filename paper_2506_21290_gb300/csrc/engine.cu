@@ -1414,6 +1414,38 @@ int mc_corr_sums(mc_handle *h, double *sums)
     return MC_OK;
 }
 
+int mc_corr_derive(int n_rows, const double *sums, const int32_t *n_atoms, double *out)
+{
+    if (n_rows < 0 || (n_rows > 0 && (!sums || !n_atoms || !out))) return fail(MC_ERR_INVALID_ARG, "bad arguments");
+    const double nan = std::nan("");
+    for (int k = 0; k < n_rows; ++k) {
+        if (n_atoms[k] < 3 || n_atoms[k] % 3 != 0) return fail(MC_ERR_INVALID_ARG, "n_atoms: a positive multiple of 3");
+        const double N = (double)n_atoms[k], M = N / 3.0;
+        const double *a = sums + (size_t)k * MC_CORR_NSUM;
+        double *o = out + (size_t)k * MC_CORR_NRES;
+        const double n = a[0];
+        o[0] = n;
+        if (!(n > 0.0)) {
+            for (int j = 1; j < MC_CORR_NRES; ++j) o[j] = nan;
+            continue;
+        }
+        const double fs = a[1] / n, fcm = a[5] / n, c2 = a[9] / n;
+        o[1] = fs;
+        o[2] = fcm;
+        o[3] = c2;
+        o[4] = N * (a[2] / n - fs * fs);
+        o[5] = M * (a[6] / n - fcm * fcm);
+        o[6] = M * (a[10] / n - c2 * c2);
+        const double fs_i = a[3] / (n * N), fcm_i = a[7] / (n * M), c2_i = a[11] / (n * M);
+        o[7] = a[4] / (n * N) - fs_i * fs_i;
+        o[8] = a[8] / (n * M) - fcm_i * fcm_i;
+        o[9] = a[12] / (n * M) - c2_i * c2_i;
+        const double den = o[9] * o[8];
+        o[10] = den > 0.0 ? (a[13] / (n * M) - c2_i * fcm_i) / std::sqrt(den) : nan;
+    }
+    return MC_OK;
+}
+
 int mc_corr_results(mc_handle *h, double *out)
 {
     if (!h || !out) return fail(MC_ERR_INVALID_ARG, "NULL argument");
@@ -1422,32 +1454,37 @@ int mc_corr_results(mc_handle *h, double *out)
     std::vector<double> S((size_t)h->n_rep * nl * MC_CORR_NSUM);
     int rc = mc_corr_sums(h, S.data());
     if (rc) return rc;
-    const double nan = std::nan("");
-    for (int r = 0; r < h->n_rep; ++r) {
-        const double N = (double)h->reps[r].n_sites, M = N / 3.0;
-        for (int l = 0; l < nl; ++l) {
-            const double *a = S.data() + ((size_t)r * nl + l) * MC_CORR_NSUM;
-            double *o = out + ((size_t)r * nl + l) * MC_CORR_NRES;
-            const double n = a[0];
-            o[0] = n;
-            if (!(n > 0.0)) {
-                for (int j = 1; j < MC_CORR_NRES; ++j) o[j] = nan;
-                continue;
+    std::vector<int32_t> N((size_t)h->n_rep * nl);
+    for (int r = 0; r < h->n_rep; ++r)
+        for (int l = 0; l < nl; ++l) N[(size_t)r * nl + l] = h->reps[r].n_sites;
+    return mc_corr_derive(h->n_rep * nl, S.data(), N.data(), out);
+}
+
+int mc_relaxation_time(int n_lags, const int64_t *lags, const double *values, const double *counts, double level,
+                       double *tau)
+{
+    if (n_lags < 1 || !lags || !values || !counts || !tau) return fail(MC_ERR_INVALID_ARG, "bad arguments");
+    *tau = std::nan("");
+    double t_prev = 0.0, f_prev = 0.0;
+    bool have_prev = false;
+    for (int l = 0; l < n_lags; ++l) {
+        if (!(counts[l] > 0.0)) continue;               // no sample at this lag
+        const double t = (double)lags[l], f = values[l];
+        if (f <= level) {
+            if (!have_prev) {
+                *tau = t;
+            } else if (t_prev > 0.0) {
+                // linear in ln t between the two lags that bracket the crossing
+                const double a = (f_prev - level) / (f_prev - f);
+                *tau = std::exp(std::log(t_prev) + a * (std::log(t) - std::log(t_prev)));
+            } else {
+                *tau = t_prev + (f_prev - level) / (f_prev - f) * (t - t_prev);
             }
-            const double fs = a[1] / n, fcm = a[5] / n, c2 = a[9] / n;
-            o[1] = fs;
-            o[2] = fcm;
-            o[3] = c2;
-            o[4] = N * (a[2] / n - fs * fs);
-            o[5] = M * (a[6] / n - fcm * fcm);
-            o[6] = M * (a[10] / n - c2 * c2);
-            const double fs_i = a[3] / (n * N), fcm_i = a[7] / (n * M), c2_i = a[11] / (n * M);
-            o[7] = a[4] / (n * N) - fs_i * fs_i;
-            o[8] = a[8] / (n * M) - fcm_i * fcm_i;
-            o[9] = a[12] / (n * M) - c2_i * c2_i;
-            const double den = o[9] * o[8];
-            o[10] = den > 0.0 ? (a[13] / (n * M) - c2_i * fcm_i) / std::sqrt(den) : nan;
+            break;
         }
+        t_prev = t;
+        f_prev = f;
+        have_prev = true;
     }
     return MC_OK;
 }
@@ -1462,30 +1499,15 @@ int mc_corr_relaxation_time(mc_handle *h, int which, double level, double *tau)
     std::vector<double> R((size_t)h->n_rep * nl * MC_CORR_NRES);
     int rc = mc_corr_results(h, R.data());
     if (rc) return rc;
+    std::vector<int64_t> lg(lags.begin(), lags.end());
+    std::vector<double> f(nl), n(nl);
     for (int r = 0; r < h->n_rep; ++r) {
-        tau[r] = std::nan("");
-        double t_prev = 0.0, f_prev = 0.0;
-        bool have_prev = false;
         for (int l = 0; l < nl; ++l) {
             const double *o = R.data() + ((size_t)r * nl + l) * MC_CORR_NRES;
-            if (!(o[0] > 0.0)) continue;               // no sample at this lag
-            const double t = (double)lags[l], f = o[1 + which];
-            if (f <= level) {
-                if (!have_prev) {
-                    tau[r] = t;
-                } else if (t_prev > 0.0) {
-                    // linear in ln t between the two lags that bracket the crossing
-                    const double a = (f_prev - level) / (f_prev - f);
-                    tau[r] = std::exp(std::log(t_prev) + a * (std::log(t) - std::log(t_prev)));
-                } else {
-                    tau[r] = t_prev + (f_prev - level) / (f_prev - f) * (t - t_prev);
-                }
-                break;
-            }
-            t_prev = t;
-            f_prev = f;
-            have_prev = true;
+            n[l] = o[0];
+            f[l] = o[1 + which];
         }
+        if ((rc = mc_relaxation_time(nl, lg.data(), f.data(), n.data(), level, tau + r))) return rc;
     }
     return MC_OK;
 }

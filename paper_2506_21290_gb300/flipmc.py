@@ -115,6 +115,8 @@ def load():
         "mc_corr_sums": ([vp, vp], i32),
         "mc_corr_results": ([vp, vp], i32),
         "mc_corr_relaxation_time": ([vp, i32, dbl, vp], i32),
+        "mc_corr_derive": ([i32, vp, vp, vp], i32),
+        "mc_relaxation_time": ([i32, vp, vp, vp, dbl, vp], i32),
         "mc_md_setup": ([vp, dbl, dbl, vp, vp, i32], i32),
         "mc_md_run": ([vp, i32], i32),
         "mc_md_state": ([vp, vp, vp], i32),
@@ -365,6 +367,26 @@ def mc_corr_results(h, n_rep, n_lags):
     out = np.zeros((n_rep, n_lags, MC_CORR_NRES), dtype=np.float64)
     _check(load().mc_corr_results(h, _ptr(out)), "mc_corr_results")
     return out
+
+
+def mc_corr_derive(sums, n_atoms):
+    """Host-only derivation of the statistics from rows of sums (..., 16) with n_atoms per row."""
+    sums = np.ascontiguousarray(sums, dtype=np.float64)
+    rows = sums.reshape(-1, MC_CORR_NSUM)
+    n_atoms = np.ascontiguousarray(np.broadcast_to(np.asarray(n_atoms, dtype=np.int32), (len(rows),)))
+    out = np.zeros((len(rows), MC_CORR_NRES), dtype=np.float64)
+    _check(load().mc_corr_derive(len(rows), _ptr(rows), _ptr(n_atoms), _ptr(out)), "mc_corr_derive")
+    return out.reshape(sums.shape[:-1] + (MC_CORR_NRES,))
+
+
+def mc_relaxation_time(lags, values, counts, level):
+    lags = np.ascontiguousarray(lags, dtype=np.int64)
+    values = np.ascontiguousarray(values, dtype=np.float64)
+    counts = np.ascontiguousarray(counts, dtype=np.float64)
+    tau = np.zeros(1, dtype=np.float64)
+    _check(load().mc_relaxation_time(len(lags), _ptr(lags), _ptr(values), _ptr(counts), float(level), _ptr(tau)),
+           "mc_relaxation_time")
+    return float(tau[0])
 
 
 def mc_corr_relaxation_time(h, which, level, n_rep):
