@@ -90,3 +90,21 @@ def test_pair_histogram_of_a_lattice():
     assert c.sum() == total
     g = S.pair_correlation(L, c, N, dr)
     assert np.all(g >= 0)
+
+
+def test_ideal_gas_g_and_S_are_one():
+    """Uniform random points: g(r) = 1 at every r (the normalisation 2 counts /
+    (N rho V_shell)), and S(q) averages to 1 over box wavevectors."""
+    rng = np.random.default_rng(11)
+    L, N = 12.0, 3000
+    q = oracle.quantize(rng.uniform(0, L, size=(N, 3)), L)
+    dr, nb = 0.25, 20
+    c = S.pair_histogram(L, q, dr, nb)
+    g = S.pair_correlation(L, c, N, dr)
+    shells = slice(4, nb)                          # r in [1, 5): enough pairs per bin for a 5% check
+    assert np.all(np.abs(g[shells] - 1.0) < 0.05)
+    assert abs(g[shells].mean() - 1.0) < 0.01
+    n = np.array([[1, 0, 0], [0, 2, 1], [3, 1, 1], [2, 2, 2], [5, 0, 1], [4, 3, 0], [1, 6, 2], [7, 1, 3]])
+    vecs = np.concatenate([n, n[:, [1, 2, 0]], n[:, [2, 0, 1]]]) * (2 * np.pi / L)
+    Sq = S.structure_factor(L, q, vecs)
+    assert abs(Sq.mean() - 1.0) < 0.35              # exponential spread, 24 vectors
