@@ -63,3 +63,39 @@ def test_two_gloo_ranks_combine_and_run_independent_replicas(tmp_path):
 def test_single_rank_combine_is_the_identity():
     import bench
     assert bench.combine_ranks(12.5, 40, 9) == (12.5, 40.0, 9.0)
+
+
+def _ensemble_rank(rank, world, port, out_dir):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        from oracle import correlation as OC
+        from paper_2506_21290_gb300 import ensemble as E
+        rng = np.random.default_rng(100 + rank)
+        M = 20
+        ss = [(rng.uniform(-0.3, 1, 3 * M), rng.uniform(-0.2, 1, M), rng.uniform(-0.5, 1, M)) for _ in range(3)]
+        res = E.ensemble_results(OC.sums_of_samples(ss), 3 * M, dist)
+        np.savez(os.path.join(out_dir, "ens%d.npz" % rank), res=res)
+        dist.barrier()
+    finally:
+        dist.destroy_process_group()
+
+
+def test_ensemble_over_two_gloo_ranks_equals_the_pooled_samples(tmp_path):
+    """Each rank holds its own samples; the all-reduced sums give the
+    statistics of all samples together (the oracle's, on the pooled list)."""
+    from oracle import correlation as OC
+    from paper_2506_21290_gb300 import build as B
+    B.build()
+    port = _free_port()
+    mp.start_processes(_ensemble_rank, args=(2, port, str(tmp_path)), nprocs=2, join=True, start_method="spawn")
+    r0 = np.load(tmp_path / "ens0.npz")["res"]
+    r1 = np.load(tmp_path / "ens1.npz")["res"]
+    assert np.array_equal(r0, r1)
+    pooled = []
+    for rank in range(2):
+        rng = np.random.default_rng(100 + rank)
+        pooled += [(rng.uniform(-0.3, 1, 60), rng.uniform(-0.2, 1, 20), rng.uniform(-0.5, 1, 20)) for _ in range(3)]
+    want = OC.stats_of_samples(pooled)
+    assert r0[0] == 6
+    assert np.allclose(r0[1:], want[1:], rtol=0, atol=1e-10)
