@@ -185,6 +185,18 @@ int mc_create(mc_handle **out, double L, int n_mol, const double *xyz, const int
 int mc_create_batch(mc_handle **out, int n_rep, const double *L, const int32_t *n_mol, const double *xyz,
                      const int32_t *types, const mc_params *params, const mc_options *opts);
 
+/*
+ * The cell grid mc_create picks for one replica (host only, no GPU): the
+ * longest interaction range (the WCA cutoff 2^(1/6) sigma_ab of any type pair
+ * and R0 sigma_ab of any pair bonded in some molecule) into *range_out
+ * (nullable), and n_c: request if it is even, >= 2 and leaves cells at least
+ * that wide, else the largest such even n_c (request = 0).  Errors:
+ * INVALID_ARG (as mc_create: sizes, types, a box smaller than twice the
+ * range, a request that makes cells too narrow).
+ */
+int mc_cell_grid(double L, int n_mol, const int32_t *types, const mc_params *params, int request, int *nc_out,
+                 double *range_out);
+
 /* Free all device memory and graphs of the handle.  NULL is ignored. */
 void mc_destroy(mc_handle *h);
 

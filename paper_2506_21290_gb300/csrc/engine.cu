@@ -913,6 +913,22 @@ int mc_pressure(mc_handle *h, const double *T, double *out)
     return check_device_errors(h);
 }
 
+int mc_cell_grid(double L, int n_mol, const int32_t *types, const mc_params *params, int request, int *nc_out,
+                 double *range_out)
+{
+    if (!types || !nc_out) return fail(MC_ERR_INVALID_ARG, "NULL argument");
+    if (n_mol < 1 || n_mol > kMaxMolecules) return fail(MC_ERR_INVALID_ARG, "n_mol outside [1, 2^27 - 2]");
+    if (!(L > 0.0) || !std::isfinite(L)) return fail(MC_ERR_INVALID_ARG, "box side must be positive");
+    for (long long i = 0; i < 3LL * n_mol; ++i)
+        if (types[i] < 0 || types[i] > 2) return fail(MC_ERR_INVALID_ARG, "type outside {0,1,2}");
+    mc_params p;
+    default_params(&p);
+    if (params) p = *params;
+    const double range = interaction_range(p, types, n_mol);
+    if (range_out) *range_out = range;
+    return choose_cells(L, range, request, nc_out);
+}
+
 int mc_structure_factor(mc_handle *h, const double *qvec, int n_q, double *out)
 {
     if (!h || !qvec || !out) return fail(MC_ERR_INVALID_ARG, "NULL argument");

@@ -107,6 +107,7 @@ def load():
         "mc_observables": ([vp, vp, i32, vp, i32, vp, vp, vp, vp], i32),
         "mc_get_info": ([vp, vp], i32),
         "mc_pressure": ([vp, vp, vp], i32),
+        "mc_cell_grid": ([dbl, i32, vp, vp, i32, vp, vp], i32),
         "mc_structure_factor": ([vp, vp, i32, vp], i32),
         "mc_pair_histogram": ([vp, dbl, i32, vp, vp], i32),
         "mc_corr_setup": ([vp, i32, vp, i32, i32, vp, i32, vp, i32], i32),
@@ -304,6 +305,17 @@ def mc_observables(h, qa, qc, n_rep, total_sites, per_particle=False):
     _check(load().mc_observables(h, _ptr(qa), len(qa), _ptr(qc), len(qc), _ptr(out), _ptr(fs), _ptr(fscm), _ptr(c2)),
            "mc_observables")
     return out, fs, fscm, c2
+
+
+def mc_cell_grid(L, types, pot, request=0):
+    """(n_c, interaction range) that mc_create picks for one replica (host only)."""
+    types = np.ascontiguousarray(types, dtype=np.int32).reshape(-1)
+    p = make_params(pot)
+    nc = C.c_int(0)
+    rng = C.c_double(0.0)
+    _check(load().mc_cell_grid(float(L), types.size // 3, _ptr(types), C.byref(p), int(request), C.byref(nc),
+                               C.byref(rng)), "mc_cell_grid")
+    return nc.value, rng.value
 
 
 def mc_pressure(h, T):
