@@ -67,6 +67,8 @@ def lib():
             L.orc_site_energy.restype = ctypes.c_double
             L.orc_phi.argtypes = [ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]
             L.orc_phi.restype = ctypes.c_double
+            L.orc_mag.argtypes = [ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]
+            L.orc_mag.restype = ctypes.c_double
             L.orc_phi_many.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                        ctypes.c_void_p, ctypes.c_void_p]
             L.orc_sweep_shift.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_void_p]
@@ -132,6 +134,14 @@ def phi(r2: float, a: int, b: int, bonded: bool, pot) -> float:
     """Pair energy of types (a, b) at squared distance r2: WCA (Eq. 1) plus, for
     a bond, FENE (Eq. 2)."""
     return lib().orc_phi(float(r2), int(a), int(b), int(bool(bonded)), _ptr(pot_array(pot)))
+
+
+def mag(r2: float, a: int, b: int, bonded: bool, pot) -> float:
+    """Conditioning scale of one pair evaluation of types (a, b) at squared
+    distance r2: the summed magnitudes 4eps s^12 + 4eps s^6 + eps of the WCA
+    pieces inside the cutoff plus, for a bond, K eps (|ln(1-x)| + x/(1-x)),
+    x = r2 / (R0 sigma_ab)^2.  The FP32 tolerances are measured against it."""
+    return lib().orc_mag(float(r2), int(a), int(b), int(bool(bonded)), _ptr(pot_array(pot)))
 
 
 def phi_many(r2: np.ndarray, a: int, b: int, bonded: bool, pot) -> np.ndarray:

@@ -622,3 +622,12 @@ void orc_phi_many(int n, const double *r2, int a, int b, int bonded, const doubl
     model_init(&md, pot);
     for (int i = 0; i < n; ++i) out[i] = phi(&md, r2[i], a, b, bonded);
 }
+
+/* Conditioning scale mag(r2) of one pair evaluation of types (a,b), for tests
+ * of its closed forms (the FP32 tolerances are measured against it). */
+double orc_mag(double r2, int a, int b, int bonded, const double *pot)
+{
+    model md;
+    model_init(&md, pot);
+    return mag(&md, r2, a, b, bonded);
+}

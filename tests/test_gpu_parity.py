@@ -129,7 +129,7 @@ FP32_DE_BOUND = 6.3e-6
 @pytest.mark.parametrize("M,seed,T,mix", [(343, 51, 1.1, W.PAPER_MIX), (216, 52, 0.75, W.RIGID_MIX),
                                           (64, 53, 2.0, W.RIGID_MIX)])
 def test_fp32_error_within_derived_bound(M, seed, T, mix):
-    """Every FP32 Delta E is within FP32_DE_BOUND x (its summed term
+    """Every FP32 Delta E is within FP32_DE_BOUND x (the oracle's summed term
     magnitudes) of the oracle's FP64 value, on the split-coordinate path and
     on the n_c = 2 raw-record path; so with the default margin no decision
     taken in FP32 can differ from the FP64 one."""
@@ -143,7 +143,9 @@ def test_fp32_error_within_derived_bound(M, seed, T, mix):
     ev = (lo["status"] == 0) & ((lg["flags"] & 1) == 0)
     assert ev.sum() > 1000
     err = np.abs(lg["dE"][ev] - lo["dE"][ev])
-    assert np.all(err <= FP32_DE_BOUND * lg["scale"][ev]), (err / lg["scale"][ev]).max()
+    # measured against the oracle's own scale (pinned to its closed forms on
+    # the CPU), not the library's
+    assert np.all(err <= FP32_DE_BOUND * lo["scale"][ev]), (err / lo["scale"][ev]).max()
 
 
 def test_energy_matches_brute_force():

@@ -114,6 +114,46 @@ def test_fene_closed_forms():
             assert math.isinf(oracle.phi(R * R, a, b, True, POT))
 
 
+def test_mag_closed_forms():
+    """The conditioning scale mag(r2) that every FP32 tolerance is measured
+    against: the summed magnitudes of the pieces of Eq. 1 (4 eps s^12,
+    4 eps s^6, eps) inside the cutoff and, for a bond, of Eq. 2
+    (K eps (|ln(1-x)| + x/(1-x))).  Closed forms at points where they are
+    simple; a dropped term, a doubled 4 eps, a missing eps factor or x in
+    place of x/(1-x) each fails one of them."""
+    sig = W.SIGMA
+    K = 33.75
+    for a in range(3):
+        for b in range(3):
+            s = 0.5 * (sig[a] + sig[b])
+            R = 1.5 * s
+            rc2 = 2.0 ** (1.0 / 3.0) * s * s
+            # r = sigma_ab: s^6 = s^12 = 1, so 4 + 4 + 1
+            assert oracle.mag(s * s, a, b, False, POT) == 9.0
+            # r^2 = y sigma_ab^2 inside the cutoff: 4 y^-6 + 4 y^-3 + 1
+            for y in (0.85, 1.1, 1.25):
+                assert oracle.mag(y * s * s, a, b, False, POT) == pytest.approx(4 * y ** -6 + 4 * y ** -3 + 1,
+                                                                               rel=1e-14)
+            # just inside the cutoff s^6 -> 1/2: 1 + 2 + 1; at and beyond it nothing
+            assert oracle.mag(rc2 * (1 - 1e-12), a, b, False, POT) == pytest.approx(4.0, rel=1e-11)
+            assert oracle.mag(rc2, a, b, False, POT) == 0.0
+            assert oracle.mag(1.3 * rc2, a, b, False, POT) == 0.0
+            # a bond beyond the WCA cutoff at 1 - x = 1/e: K (1 + (1 - 1/e) e) = K e
+            r2 = R * R * (1.0 - math.exp(-1.0))
+            assert r2 > rc2
+            assert oracle.mag(r2, a, b, True, POT) == pytest.approx(K * math.e, rel=1e-13)
+            # a bond at r = sigma_ab: both pieces, x = 1/2.25
+            x = 1.0 / 2.25
+            want = 9.0 + K * (abs(math.log(1.0 - x)) + x / (1.0 - x))
+            assert oracle.mag(s * s, a, b, True, POT) == pytest.approx(want, rel=1e-13)
+    # every piece scales with eps
+    pot2 = list(POT)
+    pot2[3] = 2.5
+    assert oracle.mag(1.0, 1, 1, False, pot2) == 9.0 * 2.5
+    r2 = 2.25 * (1.0 - math.exp(-1.0))
+    assert oracle.mag(r2, 1, 1, True, pot2) == pytest.approx(2.5 * K * math.e, rel=1e-13)
+
+
 def _random_start(M, seed=3):
     L = W.box_length(M)
     xyz, t = W.lattice_start(M, L, seed)
