@@ -131,8 +131,14 @@ typedef struct {
     uint64_t accepts[4];
     uint64_t rejected_geometry; /* MC_ST_LEFT_CELL + MC_ST_NOT_IN_CELL          */
     uint64_t rejected_bond;     /* MC_ST_BOND_BREAK                              */
-    uint64_t pair_evals;        /* candidate distances evaluated (old and new)   */
+    uint64_t pair_evals;        /* site-pair evaluations of the cell-list method: per
+                                   evaluated attempt 2 (rigid moves: 6) times the atoms
+                                   of the active cell's neighbourhood (old and new)   */
     uint64_t fp64_rechecks;     /* FP32 mode: decisions retaken in FP64          */
+    uint64_t pair_interactions; /* pair-potential evaluations inside their range, old
+                                   and new configuration counted apart: WCA terms with
+                                   r < 2^(1/6) sigma_ab and FENE terms (FP32 mode: the
+                                   FP32 pass; FP64 mode: the FP64 sum)              */
     uint64_t sweeps;
     double e_run;               /* running FP64 energy: initial + sum of accepted dE */
 } mc_stats;
@@ -476,12 +482,12 @@ int mc_autotune(mc_handle *h, int n_sweeps, const double *T, const mc_move_mix *
 int mc_get_info(mc_handle *h, mc_info *info);
 
 /*
- * Total FP64 energy (Eq. 1 + Eq. 2, every pair once) of one configuration
- * that already sits in the caller's device memory, for callers that cannot
- * allocate device memory: code running inside another framework's memory
- * pool or under a fixed device-memory budget, or code that may only enqueue
- * kernels on a stream it was given.  The paper has no counterpart; this is an
- * interface convenience.
+ * Total FP64 energy (the quantity mc_energy returns, every pair once) of one
+ * configuration that already sits in the caller's device memory, for callers
+ * that cannot allocate device memory: code running inside another framework's
+ * memory pool or under a fixed device-memory budget, or code that may only
+ * enqueue kernels on a stream it was given.  The paper has no counterpart;
+ * this is an interface convenience.
  *   L: box side; n_mol: molecules, 1 <= n_mol <= 21845 (at most 65536 atoms);
  *   dev_q: 3*3*n_mol fixed-point positions (q = floor(frac(x/L) 2^32)),
  *   dev_types: 3*n_mol types in {0,1,2}, dev_E_out: one double, all three
@@ -493,8 +499,10 @@ int mc_get_info(mc_handle *h, mc_info *info);
  * calls on a device share that array: calls whose work overlaps on the GPU
  * race and must be serialised by the caller.  The first call on a device
  * looks up the array's address and should come before any stream capture.
- * Enqueues only; the result is ready when the stream reaches it.  A type
- * outside {0,1,2} or a broken bond gives NaN (or +inf).
+ * The call only enqueues kernels and device-memory clears on the stream (it
+ * copies nothing from host memory); the result is ready when the stream
+ * reaches it.  A type outside {0,1,2} or a broken bond gives NaN (or +inf);
+ * the next valid call clears that state.
  * Errors: INVALID_ARG (sizes beyond the maximum, NULL pointers, box smaller
  * than two interaction ranges), NO_DEVICE, CUDA.
  */

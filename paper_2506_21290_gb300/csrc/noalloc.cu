@@ -84,6 +84,34 @@ int scratch_address(int dev, unsigned char **out)
     return MC_OK;
 }
 
+// The call's constants, passed by value as a kernel parameter: the call then
+// copies nothing from host memory (a copy from pageable host memory can wait
+// for the stream before it returns).
+struct Header {
+    RepInfo rep;
+    RepParam par;
+    RepCtr ctr;
+    ModelDev model;
+    int act_off[2];
+};
+
+// one block: the constants into the scratch array, the error word and the
+// per-site replica index cleared
+__global__ void noalloc_init_kernel(Header hd, unsigned char *base, int n_sites)
+{
+    if (threadIdx.x == 0) {
+        *(RepInfo *)(base + kOffRep) = hd.rep;
+        *(RepParam *)(base + kOffPar) = hd.par;
+        *(RepCtr *)(base + kOffCtr) = hd.ctr;
+        *(ModelDev *)(base + kOffModel) = hd.model;
+        ((int *)(base + kOffActOff))[0] = hd.act_off[0];
+        ((int *)(base + kOffActOff))[1] = hd.act_off[1];
+        *(int *)(base + kOffErr) = 0;
+    }
+    int *rep_of_site = (int *)(base + kOffRepOfSite);
+    for (int i = threadIdx.x; i < n_sites; i += blockDim.x) rep_of_site[i] = 0;
+}
+
 // records {q, w} in site order from the caller's arrays; a type outside
 // {0,1,2} sets the error word
 __global__ void noalloc_pack_kernel(const uint32_t *q, const int32_t *types, int n, int4 *rec, int *err)
@@ -144,13 +172,7 @@ extern "C" int mc_energy_noalloc(double L, int n_mol, const uint32_t *dev_q, con
     if (rc) return rc;
     cudaStream_t st = (cudaStream_t)stream;
 
-    struct Header {
-        RepInfo rep;
-        RepParam par;
-        RepCtr ctr;
-        ModelDev model;
-        int act_off[2];
-    } hd;
+    Header hd;
     std::memset(&hd, 0, sizeof hd);
     hd.rep.n_sites = n_sites;
     hd.rep.nc = nc;
@@ -205,13 +227,8 @@ extern "C" int mc_energy_noalloc(double L, int n_mol, const uint32_t *dev_q, con
     auto chk = [&](cudaError_t x) {
         if (e == cudaSuccess && x != cudaSuccess) e = x;
     };
-    chk(cudaMemcpyAsync(base + kOffRep, &hd.rep, sizeof(RepInfo), cudaMemcpyHostToDevice, st));
-    chk(cudaMemcpyAsync(base + kOffPar, &hd.par, sizeof(RepParam), cudaMemcpyHostToDevice, st));
-    chk(cudaMemcpyAsync(base + kOffCtr, &hd.ctr, sizeof(RepCtr), cudaMemcpyHostToDevice, st));
-    chk(cudaMemcpyAsync(base + kOffModel, &hd.model, sizeof(ModelDev), cudaMemcpyHostToDevice, st));
-    chk(cudaMemcpyAsync(base + kOffActOff, hd.act_off, sizeof(hd.act_off), cudaMemcpyHostToDevice, st));
-    chk(cudaMemsetAsync(base + kOffErr, 0, sizeof(int), st));
-    chk(cudaMemsetAsync(base + kOffRepOfSite, 0, sizeof(int) * n_sites, st));
+    noalloc_init_kernel<<<1, 256, 0, st>>>(hd, base, n_sites);
+    chk(cudaGetLastError());
     noalloc_pack_kernel<<<(n_sites + 255) / 256, 256, 0, st>>>(dev_q, dev_types, n_sites, d.rec[0], d.err);
     chk(cudaGetLastError());
     launch_cell_list(d, 0, 1, st);

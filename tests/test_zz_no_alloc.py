@@ -56,3 +56,31 @@ def test_noalloc_rejects_sizes_beyond_its_maximum():
     rc = F.mc_energy_noalloc(W.box_length(M), M, buf.data_ptr(), buf.data_ptr(), W.PAPER_POT, buf.data_ptr(), 0)
     assert rc == F.MC_ERR_INVALID_ARG
     assert "65536 atoms" in F.mc_last_error()
+
+
+def test_noalloc_invalid_type_gives_nan_and_the_next_call_is_clean():
+    """A type outside {0,1,2} poisons the result with NaN through the error
+    word; a valid call right after clears that word and agrees with
+    mc_energy again."""
+    import torch
+    from paper_2506_21290_gb300 import build as B
+    B.build()
+    M = 216
+    L = W.box_length(M)
+    xyz, t = W.lattice_start(M, L, 7)
+    h = F.Handle(L, xyz, t, W.PAPER_POT, precision="fp32")
+    E_ref = h.energy()[0]
+    dq, dt = _device_state(h)
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    bad = dt.clone()
+    bad[5] = 3
+    rc = F.mc_energy_noalloc(L, M, dq.data_ptr(), bad.data_ptr(), W.PAPER_POT, out.data_ptr(), stream.cuda_stream)
+    assert rc == F.MC_OK
+    torch.cuda.synchronize()
+    assert np.isnan(float(out.item()))
+    rc = F.mc_energy_noalloc(L, M, dq.data_ptr(), dt.data_ptr(), W.PAPER_POT, out.data_ptr(), stream.cuda_stream)
+    assert rc == F.MC_OK
+    torch.cuda.synchronize()
+    assert float(out.item()) == pytest.approx(E_ref, rel=1e-12)
+    h.close()
