@@ -5,8 +5,11 @@ A step is `--sweeps-per-step` sweeps of the whole hot path (cell-list build,
 8 checkerboard colour phases with translation and flip attempts, Metropolis,
 commit, per-sweep energy bookkeeping) followed by one FP64 total-energy
 recompute, over one synthetic configuration resident in HBM.  `value` is
-attempted MC moves per second over all ranks; site-pair evaluations per second
-and their fraction of the FP32 peak are reported next to it.
+attempted MC moves per second over all ranks in FP32 mode (FP32 pair Delta E,
+FP64 totals); site-pair evaluations per second and their fraction of the FP32
+peak are reported next to it, and the same workload is timed in FP64
+oracle-match mode (`fp64`).  The default workload is 8000 molecules at
+T = 0.75 (24000 atoms, 16^3 cells).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl native|reference]
 
@@ -33,15 +36,15 @@ from paper_2506_21290_gb300 import workloads as W  # noqa: E402
 
 METRIC = "MC attempted moves/sec and site-pair evals/sec (frac. FP32 peak), FP32 vs FP64"
 UNIT = "attempted moves/s"
-FLOPS_PER_PAIR_EVAL = 8      # 3 coordinate differences + r^2 (3 mul, 2 add)
-SM_COUNT = 152
+FLOPS_PER_PAIR_EVAL = 8      # per candidate distance: 3 scalings + r^2 (3 mul, 2 add)
+FLOPS_PER_INTERACTION = 10   # per pair-potential evaluation in range: reciprocal, s^2, s^6, s^12, combine, add
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
 L2_FLUSH_BYTES = 256 << 20
-# DRAM bytes (read + write) per launch of the dominant kernel from the ncu capture summarised in
-# profiles/sweep_persistent_single-1000_full.md; keyed by (workload, kernel, sweeps per launch), so a timed
-# launch that differs from the captured one reports null
-NCU_TRAFFIC = {("single-1000", "sweep_persistent<FP32,W=4>", 100): 267776}
+# DRAM bytes (read + write) per launch of the dominant kernel, from one ncu
+# capture of that kernel on that workload; keyed by (workload, kernel, sweeps
+# per launch), so a timed launch that differs from the captured one reports null
+NCU_TRAFFIC = {}
 
 
 def parse():
@@ -50,7 +53,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="single-1000", choices=sorted(W.WORKLOADS))
+    ap.add_argument("--workload", default="single-8000", choices=sorted(W.WORKLOADS))
     ap.add_argument("--sweeps-per-step", type=int, default=0, help="0: workload default")
     ap.add_argument("--precision", default="", choices=["", "fp32", "fp64"])
     ap.add_argument("--launch-mode", type=int, default=0, choices=[0, 1, 2],
@@ -58,6 +61,7 @@ def parse():
     ap.add_argument("--warps-per-cell", type=int, default=0, choices=[0, 1, 2, 4, 8])
     ap.add_argument("--recheck-gap", type=float, default=0.0, help="FP32 decision margin (0: library default)")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 oracle-match-mode leg")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--autotune", type=int, default=4,
@@ -162,22 +166,57 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def _cells_per_axis(L):
+    """The cell grid the library picks (largest even n_c with cells >= 1.575 wide)."""
+    nc = 2
+    while math.floor(2 ** 32 / (nc + 2)) * L / 2 ** 32 >= 1.575:
+        nc += 2
+    return nc
+
+
+def _oracle_replica(args):
+    """Worker of the all-core CPU baseline: one replica's oracle chain, whole
+    sweeps until `budget_s` has passed; returns (attempts, seconds)."""
+    L, xyz, t, T, mix, budget_s, seed = args
+    import oracle
+    ch = oracle.Chain(L, xyz, t, W.PAPER_POT, nc=_cells_per_axis(L))
+    n_sites = len(t)
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        ch.run(1, T, mix, seed=seed)
+        n += 1
+        dt = time.perf_counter() - t0
+        if dt >= budget_s:
+            return n * n_sites, dt
+
+
 def cpu_baseline(wl, name, budget_s, T, mix):
-    """The oracle, as it stands, single-threaded on this host, on a bounded sample."""
+    """The oracle, as it stands, on this host, on a bounded sample: one chain
+    on one core for a single replica; for a batch, one replica per core on
+    all cores at once (the first `cores` replicas), whole-job moves/s."""
     import oracle
     oracle.build()
     if wl["replicas"] > 1:
-        L0, M0 = float(wl["L"][0]), int(wl["n_mol"][0])
-        xyz0, t0 = wl["xyz"][: 3 * M0], wl["types"][: 3 * M0]
-        T0 = float(wl["T"][0])
-        sample_name = "replica 0 of the batch (%d molecules)" % M0
-    else:
-        L0, M0, xyz0, t0, T0 = wl["L"], wl["M_total"], wl["xyz"], wl["types"], T
-        sample_name = "%d molecules" % M0
-    nc = 2
-    while math.floor(2 ** 32 / (nc + 2)) * L0 / 2 ** 32 >= 1.575:
-        nc += 2
-    ch = oracle.Chain(L0, xyz0, t0, W.PAPER_POT, nc=nc)
+        import multiprocessing as mp
+        cores = os.cpu_count() or 1
+        n_mol = wl["n_mol"]
+        offs = np.concatenate([[0], np.cumsum(3 * n_mol)])
+        take = min(cores, len(n_mol))
+        jobs = [(float(wl["L"][k]), wl["xyz"][offs[k]:offs[k + 1]], wl["types"][offs[k]:offs[k + 1]],
+                 float(wl["T"][k]), mix, budget_s, int(wl["seeds"][k])) for k in range(take)]
+        # spawn: a forked child of a process that has touched the GPU can hang
+        with mp.get_context("spawn").Pool(take) as pool:
+            res = pool.map(_oracle_replica, jobs)
+        moves = sum(a for a, _ in res)
+        wall = max(dt for _, dt in res)
+        return {"value": moves / wall, "unit": UNIT, "cores": take, "kind": "oracle",
+                "sample": "replicas 0..%d of the batch (%d-%d molecules), one per core at once, whole sweeps for "
+                          "%.0f s each, FP64, O(N) Delta E per move" % (take - 1, int(n_mol[:take].min()),
+                                                                       int(n_mol[:take].max()), budget_s),
+                "cpu_model": _cpu_model()}
+    L0, M0, xyz0, t0, T0 = wl["L"], wl["M_total"], wl["xyz"], wl["types"], T
+    ch = oracle.Chain(L0, xyz0, t0, W.PAPER_POT, nc=_cells_per_axis(L0))
     t0w = time.perf_counter()
     ch.run(1, T0, mix, seed=1)
     one = time.perf_counter() - t0w
@@ -186,8 +225,21 @@ def cpu_baseline(wl, name, budget_s, T, mix):
     ch.run(n, T0, mix, seed=1)
     dt = time.perf_counter() - t1
     return {"value": 3 * M0 * n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "%d sweeps of %s (%s), FP64, O(N) Delta E per move, after 1 untimed sweep"
-                      % (n, sample_name, name)}
+            "sample": "%d sweeps of %d molecules (%s), FP64, O(N) Delta E per move, after 1 untimed sweep"
+                      % (n, M0, name), "cpu_model": _cpu_model()}
+
+
+def _cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            txt = f.read()
+        for key in ("model name", "CPU part"):
+            for line in txt.splitlines():
+                if line.startswith(key):
+                    return line.split(":", 1)[1].strip() + " (%s)" % os.uname().machine
+    except OSError:
+        pass
+    return os.uname().machine
 
 
 def run_reference(args):
@@ -205,10 +257,7 @@ def run_reference(args):
     else:
         M0, L0, xyz0, t0 = wl["M_total"], wl["L"], wl["xyz"], wl["types"]
         sample = "one sweep of %d molecules per step" % M0
-    nc = 2
-    while math.floor(2 ** 32 / (nc + 2)) * L0 / 2 ** 32 >= 1.575:
-        nc += 2
-    ch = oracle.Chain(L0, xyz0, t0, W.PAPER_POT, nc=nc)
+    ch = oracle.Chain(L0, xyz0, t0, W.PAPER_POT, nc=_cells_per_axis(L0))
     for _ in range(args.warmup):
         ch.run(1, T, W.PAPER_MIX, seed=1)
     t1 = time.perf_counter()
@@ -316,6 +365,83 @@ def run_md(h, wl, n_steps, stream):
     return out
 
 
+def fp32_peak_tflops(sms, mhz):
+    """FP32 peak: SMs x 128 FP32 lanes x 2 flop (fma) x clock."""
+    return sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+
+
+def timed_steps(h, wl, mix, sps, steps, stream, flush, e_dev):
+    """`steps` timed steps (the sweeps, then the FP64 energy recompute), each
+    bracketed by CUDA events on the library's stream, the L2 flushed before
+    each.  Returns (total ms, sweep-only ms, stats before, stats after)."""
+    import torch
+    h.sync()
+    torch.cuda.synchronize()
+    st0 = h.stats()
+    evs = []
+    for _ in range(steps):
+        flush.fill_(1)                 # evict the state from L2 between timed steps
+        a = torch.cuda.Event(enable_timing=True)
+        m = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        h.sweep(sps, wl["T"], mix, wl["seeds"])   # the sweep launch(es) of the step
+        m.record(stream)
+        h.energy_device(e_dev.data_ptr())         # FP64 energy recompute
+        b.record(stream)
+        evs.append((a, m, b))
+    torch.cuda.synchronize()
+    h.sync()
+    ms = sum(a.elapsed_time(b) for a, m, b in evs)
+    sweep_ms = sum(a.elapsed_time(m) for a, m, b in evs)
+    return ms, sweep_ms, st0, h.stats()
+
+
+def stat_delta(st0, st1, key):
+    return sum(s1[key] - s0[key] for s0, s1 in zip(st0, st1))
+
+
+def kernel_label(precision, info):
+    persistent = info.get("launch_mode", 0) != 1
+    return ("sweep_persistent" if persistent else "phase_kernel") + \
+        ("<FP32,W=%d>" if precision == "fp32" else "<FP64,W=%d>") % info["warps_per_cell"]
+
+
+def run_fp64_leg(F, wl, mix, sps, steps, warmup, autotune, stream, flush, sms):
+    """The same workload from the same start in FP64 oracle-match mode (every
+    Delta E the FP64 ordered sum, decisions bit-exact to the oracle's chain)."""
+    import torch
+    h = F.Handle(wl["L"], wl["xyz"], wl["types"], W.PAPER_POT, precision="fp64", n_mol=wl["n_mol"])
+    if autotune > 0:
+        h.autotune(autotune, wl["T"], mix, wl["seeds"])
+    h.set_stream(stream.cuda_stream)
+    e_dev = torch.zeros(h.n_rep, dtype=torch.float64, device="cuda")
+    for _ in range(warmup):
+        h.sweep(sps, wl["T"], mix, wl["seeds"])
+        h.energy_device(e_dev.data_ptr())
+    clocks = Clocks(torch.cuda.current_device())
+    time.sleep(0.3)
+    ms, sweep_ms, st0, st1 = timed_steps(h, wl, mix, sps, steps, stream, flush, e_dev)
+    clk = clocks.stop()
+    att = sum(sum(s1["attempts"]) - sum(s0["attempts"]) for s0, s1 in zip(st0, st1))
+    pairs = stat_delta(st0, st1, "pair_evals")
+    inter = stat_delta(st0, st1, "pair_interactions")
+    flops = FLOPS_PER_PAIR_EVAL * pairs + FLOPS_PER_INTERACTION * inter
+    info = h.info
+    out = {"value": att / (ms / 1000.0), "unit": UNIT, "ms_per_step": ms / steps, "steps": steps,
+           "sweeps_per_step": sps, "pair_evals_per_s": pairs / (ms / 1000.0),
+           "pair_interactions_per_s": inter / (ms / 1000.0),
+           "fp32_peak_frac": flops / (ms / 1000.0) / (fp32_peak_tflops(sms, SM_MAX_MHZ) * 1e12),
+           "kernel": kernel_label("fp64", info), "sweep_launch_ms": sweep_ms / steps,
+           "schedule": {"warps_per_cell": info["warps_per_cell"],
+                        "launch": "persistent" if info.get("launch_mode", 0) != 1 else "graph per sweep"},
+           "what": "FP64 oracle-match mode: every Delta E the FP64 ordered sum (unfused, fixed order), FP64 "
+                   "thresholds; same workload, start and timing as the FP32 line",
+           "clocks": clk}
+    h.close()
+    return out, (ms, att)
+
+
 def run_native(args):
     import torch
     from paper_2506_21290_gb300 import build as B
@@ -334,6 +460,7 @@ def run_native(args):
     if dist is not None:
         dist.barrier()
     F.load()
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
 
     wl = make_workload(args.workload, rank)
     precision = args.precision or wl["precision"]
@@ -355,47 +482,31 @@ def run_native(args):
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     e_dev = torch.zeros(h.n_rep, dtype=torch.float64, device="cuda")
 
-    def step():
+    for _ in range(args.warmup):
         h.sweep(sps, wl["T"], mix, wl["seeds"])
         h.energy_device(e_dev.data_ptr())
-
-    for _ in range(args.warmup):
-        step()
     h.sync()
     torch.cuda.synchronize()
-    st0 = h.stats()
     clocks = Clocks(torch.cuda.current_device())
     time.sleep(0.4)
     if dist is not None:
         dist.barrier()
-    torch.cuda.synchronize()
-    evs = []
-    for _ in range(args.steps):
-        flush.fill_(1)                 # evict the state from L2 between timed steps
-        a = torch.cuda.Event(enable_timing=True)
-        m = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        h.sweep(sps, wl["T"], mix, wl["seeds"])   # the sweep launch(es) of the step
-        m.record(stream)
-        h.energy_device(e_dev.data_ptr())         # FP64 energy recompute
-        b.record(stream)
-        evs.append((a, m, b))
-    torch.cuda.synchronize()
-    h.sync()
+    ms, sweep_ms, st0, st1 = timed_steps(h, wl, mix, sps, args.steps, stream, flush, e_dev)
+    if dist is not None:
+        dist.barrier()
     clk = clocks.stop()
-    ms = sum(a.elapsed_time(b) for a, m, b in evs)
-    sweep_ms = sum(a.elapsed_time(m) for a, m, b in evs)
-    st1 = h.stats()
     attempts = sum(sum(s1["attempts"]) - sum(s0["attempts"]) for s0, s1 in zip(st0, st1))
-    pairs = sum(s1["pair_evals"] - s0["pair_evals"] for s0, s1 in zip(st0, st1))
-    rechecks = sum(s1["fp64_rechecks"] - s0["fp64_rechecks"] for s0, s1 in zip(st0, st1))
+    pairs = stat_delta(st0, st1, "pair_evals")
+    inter = stat_delta(st0, st1, "pair_interactions")
+    rechecks = stat_delta(st0, st1, "fp64_rechecks")
     accepts = [sum(s1["accepts"][k] - s0["accepts"][k] for s0, s1 in zip(st0, st1)) for k in range(4)]
     att_k = [sum(s1["attempts"][k] - s0["attempts"][k] for s0, s1 in zip(st0, st1)) for k in range(4)]
-    geom = sum(s1["rejected_geometry"] - s0["rejected_geometry"] for s0, s1 in zip(st0, st1))
+    geom = stat_delta(st0, st1, "rejected_geometry")
     ms_max, attempts_all, pairs_all = combine_ranks(ms, attempts, pairs, dist, "cuda")
+    _, inter_all, _ = combine_ranks(ms, inter, 0, dist, "cuda")
     value = attempts_all / (ms_max / 1000.0)
     pair_rate = pairs_all / (ms_max / 1000.0)
+    flops_all = FLOPS_PER_PAIR_EVAL * pairs_all + FLOPS_PER_INTERACTION * inter_all
 
     # the dominant kernel is the sweep kernel: one persistent launch per step
     # (events around it in every timed step, on its stream); per-stage times of
@@ -403,15 +514,14 @@ def run_native(args):
     info = h.info
     persistent = info.get("launch_mode", 0) != 1
     launch_ms = sweep_ms / args.steps
-    flops_per_launch = FLOPS_PER_PAIR_EVAL * pairs / args.steps
+    flops_per_launch = (FLOPS_PER_PAIR_EVAL * pairs + FLOPS_PER_INTERACTION * inter) / args.steps
     achieved = flops_per_launch / (launch_ms / 1000.0) / 1e12
     n_prof = max(2, min(20, sps))
     stage_ms = h.sweep_timed(n_prof, wl["T"], mix, wl["seeds"])
-    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    peak_at_clock = (SM_COUNT * FP32_LANES_PER_SM * 2 * clk["sm_mhz"] * 1e6 / 1e12) if clk.get("sm_mhz") else None
+    peak = fp32_peak_tflops(sms, SM_MAX_MHZ)
+    peak_at_clock = fp32_peak_tflops(sms, clk["sm_mhz"]) if clk.get("sm_mhz") else None
 
-    kernel_name = ("sweep_persistent" if persistent else "phase_kernel") + \
-        ("<FP32,W=%d>" if precision == "fp32" else "<FP64,W=%d>") % info["warps_per_cell"]
+    kernel_name = kernel_label(precision, info)
     traffic = NCU_TRAFFIC.get((args.workload, kernel_name, sps)) if persistent else None
 
     # drift of the FP64 running total against a full FP64 recompute
@@ -427,6 +537,15 @@ def run_native(args):
         one_by_one = run_one_by_one(F, wl, mix, sps, args.one_by_one, precision)
         one_by_one["batched_over_one_by_one"] = value / one_by_one["value"]
 
+    # FP64 oracle-match mode on the same workload
+    fp64 = None
+    if precision == "fp32" and not args.no_fp64:
+        fp64, (ms64, att64) = run_fp64_leg(F, wl, mix, sps, args.steps, args.warmup, args.autotune, stream, flush,
+                                           sms)
+        ms64_max, att64_all, _ = combine_ranks(ms64, att64, 0, dist, "cuda")
+        fp64["value"] = att64_all / (ms64_max / 1000.0)
+        fp64["fp32_over_fp64"] = value / fp64["value"]
+
     # end to end through the C ABI with host buffers
     e2e = None
     if args.e2e_steps > 0:
@@ -441,7 +560,7 @@ def run_native(args):
             xyz_o, t_o, _s = h.state()
         dt = time.perf_counter() - t0
         e2e = {"value": N * sps * args.e2e_steps / dt, "unit": UNIT,
-               "h2d_bytes_per_step": int(16 * N), "d2h_bytes_per_step": int(28 * N + 8 * h.n_rep + 136 * h.n_rep),
+               "h2d_bytes_per_step": int(16 * N), "d2h_bytes_per_step": int(28 * N + 8 * h.n_rep + 144 * h.n_rep),
                "steps": args.e2e_steps,
                "path": "mc_set_state (host positions) + mc_sweep + mc_energy + mc_state (host positions)"}
 
@@ -453,7 +572,10 @@ def run_native(args):
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         cpu = cpu_baseline(wl, args.workload, args.cpu_seconds, wl["T"] if wl["replicas"] == 1 else None, mix)
-    launches_per_sweep = 4 + 8 + 1
+    # our kernels per timed step: the sweeps (one persistent launch, or per
+    # sweep 4 cell-list + 8 colour + 1 finalisation kernels in a graph) and the
+    # energy recompute (2 kernels)
+    launches_per_step = (1 if persistent else 13 * sps) + 2
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -461,17 +583,22 @@ def run_native(args):
         "data": "synthetic",
         "config": config_of(args.workload, wl, sps, precision, args.warmup, world),
         "pair_evals_per_s": pair_rate,
-        "pair_evals_fp32_peak_frac": pair_rate * FLOPS_PER_PAIR_EVAL / (peak * 1e12),
+        "pair_interactions_per_s": inter_all / (ms_max / 1000.0),
+        "pair_evals_fp32_peak_frac": flops_all / (ms_max / 1000.0) / (peak * 1e12),
+        "fp64": fp64,
         "fp64_recheck_rate": rechecks / max(attempts, 1),
         "acceptance": [accepts[k] / att_k[k] if att_k[k] else None for k in range(4)],
         "geometry_reject_rate": geom / max(attempts, 1),
         "roofline": {"bound": "alu",
                      "kernel": kernel_name,
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": traffic, "traffic_unit": "B per launch (ncu dram__bytes_read + write)", "peak_basis": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (max clock)",
+                     "traffic": traffic, "traffic_unit": "B per launch (ncu dram__bytes_read + write)",
+                     "peak_basis": "%d SMs x 128 FP32 lanes x 2 x 2070 MHz (max clock); derived, not measured" % sms,
                      "peak_at_measured_clock": peak_at_clock,
                      "launch_ms": launch_ms, "flops_per_launch": flops_per_launch,
-                     "flops_per_pair_eval": FLOPS_PER_PAIR_EVAL,
+                     "flops_basis": "%d per site-pair evaluation (2 or 6 x neighbourhood atoms per evaluated "
+                                    "attempt) + %d per pair-potential evaluation in range"
+                                    % (FLOPS_PER_PAIR_EVAL, FLOPS_PER_INTERACTION),
                      "separate_kernel_stage_ms_per_sweep": {"cell_list": stage_ms[0] / n_prof,
                                                             "8_phases": stage_ms[1] / n_prof,
                                                             "finalize": stage_ms[2] / n_prof}},
@@ -482,7 +609,7 @@ def run_native(args):
                      "launch": "persistent" if persistent else "graph per sweep",
                      "autotune": tuned},
         "one_by_one": one_by_one,
-        "gpu_launches": args.steps * ((1 + 1) if persistent else sps * launches_per_sweep) + args.steps * 2,
+        "gpu_launches": args.steps * launches_per_step,
         "clocks": clk,
     }
     if args.corr > 0:

@@ -1058,6 +1058,7 @@ int mc_state(mc_handle *h, double *xyz_out, int32_t *types_out, mc_stats *stats_
             s.rejected_bond = v[STAT_REJ_BOND];
             s.pair_evals = v[STAT_PAIRS];
             s.fp64_rechecks = v[STAT_RECHECK];
+            s.pair_interactions = v[STAT_INTER];
             s.sweeps = v[STAT_SWEEPS];
             s.e_run = e[r];
         }

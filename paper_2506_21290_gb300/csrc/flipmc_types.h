@@ -70,6 +70,7 @@ enum {
     STAT_PAIRS = 10,
     STAT_RECHECK = 11,
     STAT_SWEEPS = 12,
+    STAT_INTER = 13,    // pair-potential evaluations inside their range (WCA r < r_c, FENE), old and new
     STAT_N = 16
 };
 

@@ -200,6 +200,7 @@ struct Res {
     float scale;                // FP32 mode: sum of the term magnitudes
     double dE64;                // the FP64 Delta E (FP64 mode, or an FP32-mode recheck), else NaN
     int pairs;                  // site-pair evaluations per candidate (2 or 6)
+    int inter;                  // this lane's pair-potential evaluations inside their range
 };
 
 // what the conflict test of the later attempts of a round reads (W > 1)
@@ -213,6 +214,7 @@ struct Tally {
     unsigned att[4], acc[4], rej_geom, rej_bond, rechecks;
     float dEf;                  // FP32 mode: accepted Delta E, in commit order
     unsigned long long pairs;
+    unsigned long long inter;   // pair-potential evaluations inside their range (summed over the warp's lanes)
     double dE;                  // FP64 mode: accepted Delta E, in commit order
 };
 
@@ -339,8 +341,9 @@ struct Move {
 // does not change the sum.
 __device__ __noinline__ int dE64_ordered(const Move &mv, const RecView rv, const WarpScr S, int K, int nq,
                                          const ModelDev &md, double h, float hf, float pre_r2, int lane, int *err,
-                                         double &dE)
+                                         double &dE, int &inter)
 {
+    inter = 0;
     static_assert(QW <= 64, "a lane takes at most two queue entries");
     // the term buffers alias the queue: take the entries into registers first
     int qe0 = -1, qe1 = -1;
@@ -378,6 +381,7 @@ __device__ __noinline__ int dE64_ordered(const Move &mv, const RecView rv, const
             const double r2o = r2_fixed64(dxo, dyo, dzo, h);
             const double r2n = mv.moves_pos ? r2_fixed64(dxn, dyn, dzn, h) : r2o;
             const int abo = 3 * mv.to[k] + tj, abn = 3 * mv.tn[k] + tj;
+            inter += (r2o < md.rc2[abo]) + (r2n < md.rc2[abn]) + (bonded ? 2 : 0);
             if (bonded && !(r2n < md.R2[abn])) brk = 1;
             const double term = __dsub_rn(phi64(md, r2n, abn, bonded), phi64(md, r2o, abo, bonded));
             if (term != 0.0) {
@@ -404,6 +408,7 @@ __device__ __noinline__ int dE64_ordered(const Move &mv, const RecView rv, const
                                           (int)(mv.qo[l][2] - mv.qo[k][2]), h);
             const double r2n = r2_fixed64((int)(mv.qn[l][0] - mv.qn[k][0]), (int)(mv.qn[l][1] - mv.qn[k][1]),
                                           (int)(mv.qn[l][2] - mv.qn[k][2]), h);
+            inter += (r2o < md.rc2[ab]) + (r2n < md.rc2[ab]) + 2;
             if (!(r2n < md.R2[ab])) brk = 1;
             const double term = __dsub_rn(phi64(md, r2n, ab, true), phi64(md, r2o, ab, true));
             if (term != 0.0) {
@@ -660,6 +665,7 @@ __device__ __noinline__ int screen_mol(const Group G, const WarpScr S, int K, in
 struct Acc32 {
     float dE, mag;
     int guard;
+    int cnt;                    // pair-potential evaluations inside their range
 };
 
 __device__ __forceinline__ void add_wca(const ModelDev &md, float r2, int ab, float sign, Acc32 &a)
@@ -669,6 +675,7 @@ __device__ __forceinline__ void add_wca(const ModelDev &md, float r2, int ab, fl
         wca32(md, r2, ab, u, m);
         a.dE = fmaf(sign, u, a.dE);
         a.mag += m;
+        a.cnt += 1;
     }
 }
 
@@ -682,6 +689,7 @@ __device__ __forceinline__ void add_fene(const ModelDev &md, float r2, int ab, f
     fene32(md, r2, ab, u, m);
     a.dE = fmaf(sign, u, a.dE);
     a.mag += m;
+    a.cnt += 1;
 }
 
 // Masked forms for the hot passes: every lane evaluates every term and
@@ -692,9 +700,11 @@ __device__ __forceinline__ void wca_m(const ModelDev &md, float r2, int ab, floa
 {
     float u, m;
     wca32(md, r2, ab, u, m);
-    const float on = r2 < md.rc2f[ab] ? 1.f : 0.f;
+    const bool in = r2 < md.rc2f[ab];
+    const float on = in ? 1.f : 0.f;
     a.dE = fmaf(sign * on, u, a.dE);
     a.mag = fmaf(on, m, a.mag);
+    a.cnt += in;
 }
 
 __device__ __forceinline__ void fene_m(const ModelDev &md, float r2, int ab, float sign, bool bonded, Acc32 &a)
@@ -707,6 +717,7 @@ __device__ __forceinline__ void fene_m(const ModelDev &md, float r2, int ab, flo
     const float y = 1.0f - xs;
     const float l = __logf(y);
     const float f = on ? 1.f : 0.f;
+    a.cnt += on;
     a.dE = fmaf(sign * f, md.nkef * l, a.dE);
     a.mag = fmaf(f, md.kef * (fabsf(l) + __fdividef(xs, y) + 1.0f), a.mag);
 }
@@ -729,7 +740,7 @@ __device__ __forceinline__ int queued(const WarpScr &S, int e, int nq, int K, in
 __device__ __forceinline__ Acc32 inter_atom(const Group &G, const WarpScr &S, int nq, int lane, const ModelDev &md,
                                             int K, int k, int wi, int ti, const Q3 &qo, const Q3 &qn, float h2)
 {
-    Acc32 a{0.f, 0.f, 0};
+    Acc32 a{0.f, 0.f, 0, 0};
     const int slots = nq > 32 ? 2 : 1;   // warp-uniform
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
@@ -751,7 +762,7 @@ __device__ __forceinline__ Acc32 inter_flip(const Group &G, const WarpScr &S, in
                                             int K, int kp, int kq, int wi, int tp, int tq, const Q3 &qp,
                                             const Q3 &qq, float h2)
 {
-    Acc32 a{0.f, 0.f, 0};
+    Acc32 a{0.f, 0.f, 0, 0};
     const int slots = nq > 32 ? 2 : 1;
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
@@ -777,7 +788,7 @@ __device__ __forceinline__ Acc32 inter_flip(const Group &G, const WarpScr &S, in
 __device__ __noinline__ Acc32 inter_mol(const Group G, const WarpScr S, int nq, int lane, const ModelDev &md, int K,
                                         const int *t3, const Q3 *qo, const Q3 *qn, float h2)
 {
-    Acc32 a{0.f, 0.f, 0};
+    Acc32 a{0.f, 0.f, 0, 0};
     for (int s = 0; s < 2; ++s) {
         const int4 r = G.rec[queued(S, lane + 32 * s, nq, K, -1, -1)];
         const int tj = rec_type(r.w);
@@ -851,7 +862,7 @@ __device__ Res evaluate(const CellCtx &cx, const Group &G, const WarpScr &S, Nea
     const int wi = rk.w;
     const int mol = rec_mol(wi);
     int status = MC_ST_EVALUATED;
-    int flags = 0, accept = 0;
+    int flags = 0, accept = 0, inter = 0;
     float scale = 0.f, dE32 = 0.f;
     double dE64 = __longlong_as_double(0x7FF8000000000000ll);
 
@@ -955,8 +966,10 @@ __device__ Res evaluate(const CellCtx &cx, const Group &G, const WarpScr &S, Nea
             mv.qn[s][2] = qn[s].z;
         }
         double e64 = 0.0;
-        const int st = dE64_ordered(mv, cx.rv, S, K, nq, md, cx.h, cx.hf, cx.pre_r2, lane, cx.err, e64);
+        int cnt64 = 0;
+        const int st = dE64_ordered(mv, cx.rv, S, K, nq, md, cx.h, cx.hf, cx.pre_r2, lane, cx.err, e64, cnt64);
         dE64 = e64;
+        if (PREC == MC_PREC_FP64) inter = cnt64;
         return (st == MC_ST_EVALUATED) ? ((e64 <= thr) ? 1 : 0) : -1;
     };
 
@@ -991,6 +1004,7 @@ __device__ Res evaluate(const CellCtx &cx, const Group &G, const WarpScr &S, Nea
                 if (mvt == MC_MOVE_MOL_ROT && lane == 0) part = rot_intra32(md, ro, rn, tm, cx.hf, part);
             }
             if (qlen > QW) part.guard = 1;
+            inter = part.cnt;
             dE32 = warp_sum_f(part.dE);
             const float mag = warp_sum_f(part.mag);
             const int guard = __any_sync(FULL, part.guard);
@@ -1025,6 +1039,7 @@ __device__ Res evaluate(const CellCtx &cx, const Group &G, const WarpScr &S, Nea
     R.scale = scale;
     R.dE64 = dE64;
     R.pairs = (mvt == MC_MOVE_MOL_TRANS || mvt == MC_MOVE_MOL_ROT) ? 6 : 2;
+    R.inter = inter;
 #pragma unroll
     for (int s = 0; s < 3; ++s) {
         R.ks[s] = ks[s];
@@ -1369,6 +1384,7 @@ __device__ void run_cell(const DevState &d, int buf, int colour, const LogArgs &
     if (gt == 0) G.misc[MS_PHASE] = (int)(parity ^ 1u);   // every thread has read the parity
 
     Tally t{};
+    unsigned inter_lane = 0;           // this lane's share of the committed attempts' in-range evaluations
     for (int a0 = 0; a0 < n; a0 += 32) {
         if (a0 > 0) {
             // random words and thresholds of the next chunk (cells with more than 32 atoms)
@@ -1419,6 +1435,7 @@ __device__ void run_cell(const DevState &d, int buf, int colour, const LogArgs &
             }
             // committed attempts touch different molecules: each warp applies its own
             if (wig < adv && lane == 0) commit<PREC>(G, R, a + wig, K, t, lg, ri, ct.sweep, own_start);
+            if (wig < adv) inter_lane += (unsigned)R.inter;
             if constexpr (W > 1) gsync<W>(gid);
             else __syncwarp();
             a += adv;
@@ -1441,6 +1458,9 @@ __device__ void run_cell(const DevState &d, int buf, int colour, const LogArgs &
         }
         dst[kk] = nw;
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) inter_lane += __shfl_xor_sync(FULL, inter_lane, o);
+    t.inter = inter_lane;
     // ---- publish the cell to the neighbours waiting for it (before the
     // counts, which nobody waits for); then the warps' tallies in warp order ----
     if constexpr (W > 1) {
@@ -1462,6 +1482,7 @@ __device__ void run_cell(const DevState &d, int buf, int colour, const LogArgs &
                 t.rej_bond += u.rej_bond;
                 t.rechecks += u.rechecks;
                 t.pairs += u.pairs;
+                t.inter += u.inter;
                 if (PREC == MC_PREC_FP64) t.dE = __dadd_rn(t.dE, u.dE);
                 else t.dEf += u.dEf;
             }
@@ -1476,6 +1497,7 @@ __device__ void run_cell(const DevState &d, int buf, int colour, const LogArgs &
         if (t.rej_geom) atomicAdd(st + STAT_REJ_GEOM, (unsigned long long)t.rej_geom);
         if (t.rej_bond) atomicAdd(st + STAT_REJ_BOND, (unsigned long long)t.rej_bond);
         if (t.pairs) atomicAdd(st + STAT_PAIRS, t.pairs);
+        if (t.inter) atomicAdd(st + STAT_INTER, t.inter);
         if (t.rechecks) atomicAdd(st + STAT_RECHECK, (unsigned long long)t.rechecks);
     }
 }

@@ -55,7 +55,7 @@ class mc_options(C.Structure):
 class mc_stats(C.Structure):
     _fields_ = [("attempts", C.c_uint64 * 4), ("accepts", C.c_uint64 * 4), ("rejected_geometry", C.c_uint64),
                 ("rejected_bond", C.c_uint64), ("pair_evals", C.c_uint64), ("fp64_rechecks", C.c_uint64),
-                ("sweeps", C.c_uint64), ("e_run", C.c_double)]
+                ("pair_interactions", C.c_uint64), ("sweeps", C.c_uint64), ("e_run", C.c_double)]
 
 
 class mc_info(C.Structure):
@@ -447,7 +447,7 @@ def mc_energy_noalloc(L, n_mol, dev_q_ptr, dev_types_ptr, pot, dev_out_ptr, stre
 def stats_dict(s):
     return {"attempts": list(s.attempts), "accepts": list(s.accepts), "rejected_geometry": s.rejected_geometry,
             "rejected_bond": s.rejected_bond, "pair_evals": s.pair_evals, "fp64_rechecks": s.fp64_rechecks,
-            "sweeps": s.sweeps, "e_run": s.e_run}
+            "pair_interactions": s.pair_interactions, "sweeps": s.sweeps, "e_run": s.e_run}
 
 
 class Handle:
