@@ -114,7 +114,15 @@ typedef struct {
  * cells); results do not depend on it.  launch_mode: 0 = one persistent
  * cooperative launch per mc_sweep call when the device supports it, else a
  * CUDA graph per sweep; 1 = graphs; 2 = persistent (INVALID_ARG if
- * unsupported). */
+ * unsupported).  recompute_every: k > 0 makes every k-th sweep of
+ * mc_sweep / mc_sweep_batch / mc_corr_run (counted across calls) end with an
+ * FP64 recompute of each replica's total energy on the device: the relative
+ * drift |e_run - E| / |E| of the running total is recorded in mc_stats and
+ * e_run restarts from E (0 = off; the chain itself is unchanged).
+ * wait_limit_log2: 0 = the
+ * default bounds of the device-side waits between blocks; 1..30 = every such
+ * wait gives up after 2^k polls and reports MC_ERR_TIMEOUT (for tests of the
+ * timeout path; a wait that gives up leaves the state undefined). */
 typedef struct {
     int precision;
     int n_cells;
@@ -123,6 +131,8 @@ typedef struct {
     double recheck_gap;
     int warps_per_cell;
     int launch_mode;
+    int recompute_every;
+    int wait_limit_log2;
 } mc_options;
 
 /* Per-replica counters since creation (or mc_reset_stats). */
@@ -141,6 +151,9 @@ typedef struct {
                                    FP32 pass; FP64 mode: the FP64 sum)              */
     uint64_t sweeps;
     double e_run;               /* running FP64 energy: initial + sum of accepted dE */
+    uint64_t recomputes;        /* FP64 recomputes made by recompute_every           */
+    double drift_last;          /* relative drift |e_run - E| / |E| at the last one  */
+    double drift_max;           /* largest such drift                                */
 } mc_stats;
 
 /* Static facts of a handle. */
@@ -156,6 +169,7 @@ typedef struct {
     int active_cells_per_colour;
     int launch_mode;          /* 1: a CUDA graph per sweep; 2: one persistent launch per call */
     int persistent_blocks;    /* blocks of the persistent launch (0 with graphs) */
+    int recompute_every;      /* as in mc_options */
 } mc_info;
 
 /* One attempted move as recorded by mc_sweep_logged(). */
@@ -323,7 +337,7 @@ int mc_set_state_fixed(mc_handle *h, const uint32_t *q, const int64_t *X, const 
  * (seed, sweep, cell, attempt), so resuming reproduces an uninterrupted run. */
 int mc_set_sweep(mc_handle *h, uint64_t sweep);
 
-/* Clear the counters of mc_stats (not e_run). */
+/* Clear the counters of mc_stats (not e_run), the drift figures included. */
 int mc_reset_stats(mc_handle *h);
 
 /*
@@ -508,6 +522,16 @@ int mc_get_info(mc_handle *h, mc_info *info);
  */
 int mc_energy_noalloc(double L, int n_mol, const uint32_t *dev_q, const int32_t *dev_types, const mc_params *params,
                       double *dev_E_out, void *stream);
+
+/*
+ * Test hook for the library's failure paths (the paper has no counterpart):
+ * after this call, the device allocation number `after` (0 = the next one)
+ * made by mc_create / mc_create_batch fails as if the device were out of
+ * memory; that call then frees what it had allocated and returns
+ * MC_ERR_CUDA.  The hook disarms itself once it has fired; after < 0 disarms
+ * it.  Process-wide; not meant for production use.
+ */
+void mc_test_fail_alloc(int after);
 
 /* Message describing the calling thread's last error ("" if none). */
 const char *mc_last_error(void);

@@ -85,6 +85,27 @@ void launch_energy(const DevState &d, int buf, double *e_site, double *e_out_dev
     replica_sum_kernel<<<d.n_rep, 256, 0, st>>>(d, e_site, 0, 0.0, e_out_dev, 1, 0);
 }
 
+// Drift check of the running total against a fresh FP64 recompute E, per
+// replica (one thread each): the relative drift |e_run - E| / |E| into
+// drift[2r] (last) and drift[2r + 1] (largest so far), one more recompute
+// counted, and e_run restarted from E.
+__global__ void drift_kernel(DevState d, const double *E, double *drift)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= d.n_rep) return;
+    const double e = E[r];
+    const double rel = fabs(d.e_run[r] - e) / fabs(e);
+    drift[2 * r] = rel;
+    drift[2 * r + 1] = fmax(drift[2 * r + 1], rel);
+    d.stats[(size_t)r * STAT_N + STAT_RECOMP] += 1;
+    d.e_run[r] = e;
+}
+
+void launch_drift(const DevState &d, const double *E, double *drift, cudaStream_t st)
+{
+    drift_kernel<<<(d.n_rep + 127) / 128, 128, 0, st>>>(d, E, drift);
+}
+
 void launch_virial(const DevState &d, int buf, double *w_site, double *w_out_dev, cudaStream_t st)
 {
     pair_sites_kernel<true><<<(d.n_sites + 255) / 256, 256, 0, st>>>(d, buf, w_site);

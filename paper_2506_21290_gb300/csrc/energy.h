@@ -16,6 +16,9 @@ struct ObsState {
 
 // FP64 energy per replica into e_out_dev[n_rep]; e_site is n_sites scratch.
 void launch_energy(const DevState &d, int buf, double *e_site, double *e_out_dev, cudaStream_t st);
+// Periodic drift check: drift[2r] = |e_run - E| / |E| (last), drift[2r+1] its
+// largest value; one recompute counted; e_run restarts from E[r].
+void launch_drift(const DevState &d, const double *E, double *drift, cudaStream_t st);
 // S(q) per (replica, wavevector): out[r * n_q + k] = |sum_i exp(i q_k . x_i)|^2 / N.
 void launch_sq(const DevState &d, const long long *X, const double *qv, int n_q, double *out, cudaStream_t st);
 // Pair-distance counts per replica and bin (every pair once); counts zeroed by the caller.

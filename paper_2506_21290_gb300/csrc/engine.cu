@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -61,6 +62,9 @@ struct Buf {
     size_t bytes = 0;
 };
 
+// mc_test_fail_alloc: allocations left before the one that fails (-1: off)
+std::atomic<int> g_fail_alloc{-1};
+
 }  // namespace
 
 struct mc_handle {
@@ -78,6 +82,9 @@ struct mc_handle {
     int *d_scan_tot = nullptr;           // per-block scan totals of the persistent sweep
     int wpb = 4;
     double recheck_gap = 1e-5;
+    int recompute_every = 0;             // FP64 recompute every k sweeps of sweep_impl (0: off)
+    int since_recompute = 0;             // sweeps made since the last one
+    double *d_drift = nullptr;           // per replica: last and largest relative drift
     mc_params params{};
     std::vector<RepInfo> reps;
     std::vector<int> mol_off;
@@ -131,6 +138,11 @@ struct mc_handle {
     {
         void *q = nullptr;
         const size_t bytes = std::max<size_t>(n, 1) * sizeof(T);
+        if (g_fail_alloc == 0) {
+            g_fail_alloc = -1;
+            return fail(MC_ERR_CUDA, "cudaMalloc: out of memory (injected by mc_test_fail_alloc)");
+        }
+        if (g_fail_alloc > 0) --g_fail_alloc;
         cudaError_t e = cudaMalloc(&q, bytes);
         if (e != cudaSuccess) return fail(MC_ERR_CUDA, std::string("cudaMalloc: ") + cudaGetErrorString(e));
         cudaMemset(q, 0, bytes);
@@ -419,6 +431,8 @@ int create_impl(mc_handle **out, int n_rep, const double *L, const int32_t *n_mo
     if (opts) o = *opts;
     if (o.precision != MC_PREC_FP32 && o.precision != MC_PREC_FP64) return fail(MC_ERR_INVALID_ARG, "precision");
     if (o.device < 0 || o.device >= ndev) return fail(MC_ERR_INVALID_ARG, "device ordinal");
+    if (o.recompute_every < 0) return fail(MC_ERR_INVALID_ARG, "recompute_every < 0");
+    if (o.wait_limit_log2 < 0 || o.wait_limit_log2 > 30) return fail(MC_ERR_INVALID_ARG, "wait_limit_log2");
     mc_params p;
     default_params(&p);
     if (params) p = *params;
@@ -431,6 +445,7 @@ int create_impl(mc_handle **out, int n_rep, const double *L, const int32_t *n_mo
     h->precision = o.precision;
     h->params = p;
     h->recheck_gap = o.recheck_gap > 0.0 ? o.recheck_gap : 1e-5;
+    h->recompute_every = o.recompute_every;
     h->n_rep = n_rep;
     build_model(p, h->recheck_gap, h->model_host);
 
@@ -531,6 +546,7 @@ int create_impl(mc_handle **out, int n_rep, const double *L, const int32_t *n_mo
     d.stencil_cap = cap;
     d.own_cap = h->own_cap;
     d.precision = h->precision;
+    d.wait_limit = o.wait_limit_log2 > 0 ? (1u << o.wait_limit_log2) : 0u;
     const int M_tot = h->n_sites / 3;
     int4 *r0, *r1;
     int *cc, *cs, *co, *so, *img, *err;
@@ -552,7 +568,7 @@ int create_impl(mc_handle **out, int n_rep, const double *L, const int32_t *n_mo
         (rc = h->alloc(&h->d_obs_out, 3 * (size_t)n_rep)) ||
         (rc = h->alloc(&h->ds.att_rnd, 2 * (size_t)h->n_sites)) || (rc = h->alloc(&h->d_bar, 2)) ||
         (rc = h->alloc(&h->ds.cell_done, h->n_cells)) || (rc = h->alloc(&h->ds.cell_count2, h->n_cells)) ||
-        (rc = h->alloc(&h->d_scan_tot, kMaxPersistentBlocks)) ||
+        (rc = h->alloc(&h->d_scan_tot, kMaxPersistentBlocks)) || (rc = h->alloc(&h->d_drift, 2 * (size_t)n_rep)) ||
         (rc = h->precision == MC_PREC_FP64 ? h->alloc(&h->ds.att_thr64, h->n_sites)
                                            : h->alloc(&h->ds.att_thr32, h->n_sites))) {
         mc_destroy(h);
@@ -676,21 +692,33 @@ static int sweep_impl(mc_handle *h, int n_sweeps, const double *T, const mc_move
     if (rc) return rc;
     if ((rc = set_device(h))) return rc;
     if ((rc = upload_params(h, T, mix, seeds, same))) return rc;
-    if (n_sweeps == 0) return MC_OK;
-    if (h->pgrid > 0) {
-        // all sweeps of the call in one cooperative launch (which expects zero
-        // counts in cell_count on entry and clears cell_count2 itself)
-        CUDA_TRY(cudaMemsetAsync(h->ds.cell_count, 0, sizeof(int) * h->n_cells, h->stream));
-        CUDA_TRY(cudaMemsetAsync(h->d_bar, 0, sizeof(unsigned int) * 2, h->stream));
-        CUDA_TRY(cudaMemsetAsync(h->ds.cell_done, 0, sizeof(unsigned int) * h->n_cells, h->stream));
-        const int e = launch_persistent(h->ds, h->cur, n_sweeps, h->wpb, h->pgrid, h->d_bar, h->d_scan_tot, h->stream);
-        if (e != 0) return fail(MC_ERR_CUDA, std::string("persistent sweep launch: ") + cudaGetErrorString((cudaError_t)e));
-        h->cur ^= (n_sweeps & 1);
-    } else {
-        for (int s = 0; s < n_sweeps; ++s) {
-            if ((rc = ensure_graph(h, h->cur))) return rc;
-            CUDA_TRY(cudaGraphLaunch(h->graph[h->cur], h->stream));
-            h->cur ^= 1;
+    while (n_sweeps > 0) {
+        // the sweeps up to the next periodic FP64 recompute (all of them when off)
+        const int chunk =
+            h->recompute_every > 0 ? std::min(n_sweeps, h->recompute_every - h->since_recompute) : n_sweeps;
+        if (h->pgrid > 0) {
+            // all sweeps of the chunk in one cooperative launch (which expects
+            // zero counts in cell_count on entry and clears cell_count2 itself)
+            CUDA_TRY(cudaMemsetAsync(h->ds.cell_count, 0, sizeof(int) * h->n_cells, h->stream));
+            CUDA_TRY(cudaMemsetAsync(h->d_bar, 0, sizeof(unsigned int) * 2, h->stream));
+            CUDA_TRY(cudaMemsetAsync(h->ds.cell_done, 0, sizeof(unsigned int) * h->n_cells, h->stream));
+            const int e = launch_persistent(h->ds, h->cur, chunk, h->wpb, h->pgrid, h->d_bar, h->d_scan_tot, h->stream);
+            if (e != 0)
+                return fail(MC_ERR_CUDA, std::string("persistent sweep launch: ") + cudaGetErrorString((cudaError_t)e));
+            h->cur ^= (chunk & 1);
+        } else {
+            for (int s = 0; s < chunk; ++s) {
+                if ((rc = ensure_graph(h, h->cur))) return rc;
+                CUDA_TRY(cudaGraphLaunch(h->graph[h->cur], h->stream));
+                h->cur ^= 1;
+            }
+        }
+        n_sweeps -= chunk;
+        if (h->recompute_every > 0 && (h->since_recompute += chunk) >= h->recompute_every) {
+            // FP64 total from the state, drift of the running total, restart from it
+            if ((rc = enqueue_energy(h))) return rc;
+            launch_drift(h->ds, h->d_e_out, h->d_drift, h->stream);
+            h->since_recompute = 0;
         }
     }
     CUDA_TRY(cudaGetLastError());
@@ -819,6 +847,10 @@ int mc_autotune(mc_handle *h, int n_sweeps, const double *T, const mc_move_mix *
         h->cur = cur0;
     };
     copy_all(true);
+    // the trial sweeps make no periodic recompute (the drift figures and the
+    // recompute count stay as they are)
+    const int every0 = h->recompute_every, since0 = h->since_recompute;
+    h->recompute_every = 0;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -853,6 +885,8 @@ int mc_autotune(mc_handle *h, int n_sweeps, const double *T, const mc_move_mix *
         }
     }
     copy_all(false);
+    h->recompute_every = every0;
+    h->since_recompute = since0;
     rc = set_schedule(h, bestW, bestP);
     cudaStreamSynchronize(h->stream);
     cudaEventDestroy(e0);
@@ -1042,10 +1076,11 @@ int mc_state(mc_handle *h, double *xyz_out, int32_t *types_out, mc_stats *stats_
     }
     if (stats_out) {
         std::vector<unsigned long long> st((size_t)STAT_N * h->n_rep);
-        std::vector<double> e(h->n_rep);
+        std::vector<double> e(h->n_rep), dr(2 * (size_t)h->n_rep);
         CUDA_TRY(cudaMemcpyAsync(st.data(), h->ds.stats, sizeof(unsigned long long) * st.size(), cudaMemcpyDeviceToHost,
                                  h->stream));
         CUDA_TRY(cudaMemcpyAsync(e.data(), h->ds.e_run, sizeof(double) * h->n_rep, cudaMemcpyDeviceToHost, h->stream));
+        CUDA_TRY(cudaMemcpyAsync(dr.data(), h->d_drift, sizeof(double) * dr.size(), cudaMemcpyDeviceToHost, h->stream));
         CUDA_TRY(cudaStreamSynchronize(h->stream));
         for (int r = 0; r < h->n_rep; ++r) {
             mc_stats &s = stats_out[r];
@@ -1061,6 +1096,9 @@ int mc_state(mc_handle *h, double *xyz_out, int32_t *types_out, mc_stats *stats_
             s.pair_interactions = v[STAT_INTER];
             s.sweeps = v[STAT_SWEEPS];
             s.e_run = e[r];
+            s.recomputes = v[STAT_RECOMP];
+            s.drift_last = dr[2 * (size_t)r];
+            s.drift_max = dr[2 * (size_t)r + 1];
         }
         return check_device_errors(h);
     }
@@ -1138,6 +1176,7 @@ int mc_reset_stats(mc_handle *h)
     int rc = set_device(h);
     if (rc) return rc;
     CUDA_TRY(cudaMemsetAsync(h->ds.stats, 0, sizeof(unsigned long long) * STAT_N * h->n_rep, h->stream));
+    CUDA_TRY(cudaMemsetAsync(h->d_drift, 0, sizeof(double) * 2 * h->n_rep, h->stream));
     CUDA_TRY(cudaStreamSynchronize(h->stream));
     return MC_OK;
 }
@@ -1715,10 +1754,16 @@ int mc_get_info(mc_handle *h, mc_info *info)
     info->active_cells_per_colour = h->n_act;
     info->launch_mode = h->pgrid > 0 ? 2 : 1;
     info->persistent_blocks = h->pgrid;
+    info->recompute_every = h->recompute_every;
     return MC_OK;
 }
 
 }  // extern "C"
+
+extern "C" void mc_test_fail_alloc(int after)
+{
+    g_fail_alloc = after < 0 ? -1 : after;
+}
 
 int flipmc::record_error(int code, const char *msg)
 {

@@ -71,6 +71,7 @@ enum {
     STAT_RECHECK = 11,
     STAT_SWEEPS = 12,
     STAT_INTER = 13,    // pair-potential evaluations inside their range (WCA r < r_c, FENE), old and new
+    STAT_RECOMP = 14,   // FP64 recomputes of the total energy (recompute_every)
     STAT_N = 16
 };
 
@@ -90,6 +91,7 @@ struct DevState {
     int stencil_cap;     // atoms staged per neighbourhood (plus kPadSlots padding candidates)
     int own_cap;         // atoms of the own cell a neighbourhood may hold
     int precision;
+    unsigned wait_limit; // polls after which a wait between blocks gives up (0: the defaults)
     const RepInfo *rep;
     const RepParam *par;
     RepCtr *ctr;

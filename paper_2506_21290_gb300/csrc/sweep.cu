@@ -184,9 +184,8 @@ __device__ __forceinline__ void bulk_to_smem(void *dst, const void *src, unsigne
 // per warp: interaction queue, and (aliased, used after it) the FP64 term buffers
 struct WarpScr {
     int *qc;                    // [QW + 1] queued candidate indices, then a slot that takes discarded writes
-    unsigned long long *key;    // [TERM_CAP]
+    unsigned long long *key;    // [TERM_CAP] term keys; after ranking, the values in key order (as doubles)
     double *val;                // [TERM_CAP]
-    double *sorted;             // [TERM_CAP]
     int *cnt;                   // [4]
 };
 
@@ -242,7 +241,7 @@ __host__ __device__ inline size_t warp_scr_bytes()
 {
     const size_t q = al16(sizeof(int) * (QW + 1));
     const size_t k = al16(sizeof(unsigned long long) * TERM_CAP);
-    return (q > k ? q : k) + 2 * al16(sizeof(double) * TERM_CAP) + al16(sizeof(int) * 4);
+    return (q > k ? q : k) + al16(sizeof(double) * TERM_CAP) + al16(sizeof(int) * 4);
 }
 
 __host__ __device__ inline size_t group_bytes(int cap, int own_cap, int W)
@@ -287,8 +286,7 @@ __device__ inline WarpScr warp_scr(const Group &G, int wig)
     s.qc = (int *)b;
     s.key = (unsigned long long *)b;    // aliases the queue: used only after it
     s.val = (double *)(b + qk);
-    s.sorted = (double *)(b + qk + al16(sizeof(double) * TERM_CAP));
-    s.cnt = (int *)(b + qk + 2 * al16(sizeof(double) * TERM_CAP));
+    s.cnt = (int *)(b + qk + al16(sizeof(double) * TERM_CAP));
     return s;
 }
 
@@ -428,16 +426,32 @@ __device__ __noinline__ int dE64_ordered(const Move &mv, const RecView rv, const
         dE = __longlong_as_double(0x7FF8000000000000ll);
         return MC_ST_EVALUATED;
     }
-    for (int e = lane; e < nt; e += 32) {
-        const unsigned long long key = S.key[e];
-        int rank = 0;
-        for (int f = 0; f < nt; ++f) rank += S.key[f] < key;
-        S.sorted[rank] = S.val[e];
+    // rank every term by its key (keys are distinct), then put the values in
+    // key order over the key array and sum them in that order
+    static_assert(TERM_CAP <= 128, "a lane ranks at most four terms");
+    unsigned long long kk[4];
+    double vv[4];
+    int rk[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        const int e = lane + 32 * s;
+        kk[s] = e < nt ? S.key[e] : ~0ull;
+        vv[s] = e < nt ? S.val[e] : 0.0;
     }
+    for (int f = 0; f < nt; ++f) {
+        const unsigned long long kf = S.key[f];
+#pragma unroll
+        for (int s = 0; s < 4; ++s) rk[s] += kf < kk[s];
+    }
+    __syncwarp();
+    double *sorted = (double *)S.key;
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+        if (lane + 32 * s < nt) sorted[rk[s]] = vv[s];
     __syncwarp();
     double s = 0.0;
     if (lane == 0)
-        for (int e = 0; e < nt; ++e) s = __dadd_rn(s, S.sorted[e]);
+        for (int e = 0; e < nt; ++e) s = __dadd_rn(s, sorted[e]);
     dE = __shfl_sync(FULL, s, 0);
     __syncwarp();
     return brk ? MC_ST_BOND_BREAK : MC_ST_EVALUATED;
@@ -1184,8 +1198,9 @@ __device__ __forceinline__ void init_group(unsigned char *gsmem, const DevState 
 // visible, and none of them still reads this cell's atoms; neighbours of a
 // larger colour wait for this cell in turn).  done[c] counts the phases cell c
 // completed in the launch; dep = s + 1 (0: ordered by kernel boundaries).
-__device__ __forceinline__ void wait_done(const unsigned int *done, unsigned dep, int *err)
+__device__ __forceinline__ void wait_done(const unsigned int *done, unsigned dep, int *err, unsigned limit)
 {
+    const unsigned lim = limit ? limit : (1u << 21);
     unsigned spins = 0;
     for (;;) {
         unsigned v;
@@ -1194,7 +1209,7 @@ __device__ __forceinline__ void wait_done(const unsigned int *done, unsigned dep
         ++spins;
         // bounded; and once any wait of the launch has given up, the others stop too
         if ((spins & 4095u) == 0 && (*(volatile int *)err & ERR_TIMEOUT)) return;
-        if (spins > (1u << 21)) {
+        if (spins > lim) {
             atomicOr(err, ERR_TIMEOUT);
             return;
         }
@@ -1271,7 +1286,7 @@ __device__ void run_cell(const DevState &d, int buf, int colour, const LogArgs &
                 else th32 = d.att_thr32[slot];
             }
         }
-        if (wait_c >= 0) wait_done(d.cell_done + wait_c, dep, d.err);
+        if (wait_c >= 0) wait_done(d.cell_done + wait_c, dep, d.err, d.wait_limit);
         int incl = cnt;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -1575,8 +1590,9 @@ struct GridBar {
 // above it) and the polls are acquires (the block's reads after the
 // __syncthreads below see every other block's published writes).  The wait is
 // bounded.
-__device__ bool grid_sync(const GridBar &gb, unsigned int &target, int *err)
+__device__ bool grid_sync(const GridBar &gb, unsigned int &target, int *err, unsigned limit)
 {
+    const unsigned long long lim = limit ? limit : (1ull << 23);
     __shared__ int ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -1593,7 +1609,7 @@ __device__ bool grid_sync(const GridBar &gb, unsigned int &target, int *err)
                 ok = 0;
                 break;
             }
-            if (spins > (1ull << 23)) {
+            if (spins > lim) {
                 atomicOr(err, ERR_TIMEOUT);
                 ok = 0;
                 break;
@@ -1664,7 +1680,7 @@ __global__ void __launch_bounds__(block_threads<W>(), W == 1 ? 3 : 1) sweep_pers
         for (int g = tid; g < d.n_sites; g += nthr) cl_count_item(d, buf, g, sweep0, d.cell_count);
     for (int s = 0; s < n_sweeps; ++s) {
         int *const cnt = (s & 1) ? d.cell_count2 : d.cell_count;
-        if (!grid_sync(gb, bar_target, d.err)) return;
+        if (!grid_sync(gb, bar_target, d.err, d.wait_limit)) return;
         // ---- exclusive scan: chunk totals, then each block scans its chunk ----
         {
             int sum = 0;
@@ -1673,7 +1689,7 @@ __global__ void __launch_bounds__(block_threads<W>(), W == 1 ? 3 : 1) sweep_pers
             block_excl_scan<NT>(sum, tmp, total);
             if (threadIdx.x == 0) gb.scan_tot[blockIdx.x] = total;
         }
-        if (!grid_sync(gb, bar_target, d.err)) return;
+        if (!grid_sync(gb, bar_target, d.err, d.wait_limit)) return;
         {
             int off = 0, all = 0;
             for (int b = threadIdx.x; b < (int)gridDim.x; b += NT) {
@@ -1695,22 +1711,22 @@ __global__ void __launch_bounds__(block_threads<W>(), W == 1 ? 3 : 1) sweep_pers
             }
             if (blockIdx.x == 0 && threadIdx.x == 0) d.cell_start[nC] = t2;
         }
-        if (!grid_sync(gb, bar_target, d.err)) return;
+        if (!grid_sync(gb, bar_target, d.err, d.wait_limit)) return;
         // ---- scatter (and clear the counts the next sweep will use, last read
         // by the previous sweep's scan), then order each cell and draw its
         // attempts' random numbers ----
         for (int g = tid; g < d.n_sites; g += nthr) cl_scatter_item(d, buf, buf ^ 1, g);
         for (int c = tid; c < nC; c += nthr) ((s & 1) ? d.cell_count : d.cell_count2)[c] = 0;
-        if (!grid_sync(gb, bar_target, d.err)) return;
+        if (!grid_sync(gb, bar_target, d.err, d.wait_limit)) return;
         for (int c = blockIdx.x * (NT / 32) + warp; c < nC; c += gridDim.x * (NT / 32))
             cl_order_cell(d, buf ^ 1, c, lane);
-        if (!grid_sync(gb, bar_target, d.err)) return;
+        if (!grid_sync(gb, bar_target, d.err, d.wait_limit)) return;
         // ---- the 8 colours, ordered cell by cell (no grid-wide barrier between
         // colours: each cell waits for its neighbours of smaller colours) ----
         for (int colour = 0; colour < 8; ++colour)
             for (int g = blockIdx.x * CPB + gid; g < d.n_act; g += gridDim.x * CPB)
                 run_cell<PREC, W>(d, buf ^ 1, colour, none, g, md, mx, gsmem, gid, (unsigned)s + 1u);
-        if (!grid_sync(gb, bar_target, d.err)) return;
+        if (!grid_sync(gb, bar_target, d.err, d.wait_limit)) return;
         // ---- finalise the sweep and, in the same stage, count the next
         // sweep's cell list (it reads only the positions written back above,
         // and the shift of sweep s + 1; the finalisation does not touch the

@@ -49,20 +49,22 @@ class mc_move_mix(C.Structure):
 
 class mc_options(C.Structure):
     _fields_ = [("precision", C.c_int), ("n_cells", C.c_int), ("device", C.c_int), ("stencil_cap", C.c_int),
-                ("recheck_gap", C.c_double), ("warps_per_cell", C.c_int), ("launch_mode", C.c_int)]
+                ("recheck_gap", C.c_double), ("warps_per_cell", C.c_int), ("launch_mode", C.c_int),
+                ("recompute_every", C.c_int), ("wait_limit_log2", C.c_int)]
 
 
 class mc_stats(C.Structure):
     _fields_ = [("attempts", C.c_uint64 * 4), ("accepts", C.c_uint64 * 4), ("rejected_geometry", C.c_uint64),
                 ("rejected_bond", C.c_uint64), ("pair_evals", C.c_uint64), ("fp64_rechecks", C.c_uint64),
-                ("pair_interactions", C.c_uint64), ("sweeps", C.c_uint64), ("e_run", C.c_double)]
+                ("pair_interactions", C.c_uint64), ("sweeps", C.c_uint64), ("e_run", C.c_double),
+                ("recomputes", C.c_uint64), ("drift_last", C.c_double), ("drift_max", C.c_double)]
 
 
 class mc_info(C.Structure):
     _fields_ = [("n_rep", C.c_int), ("precision", C.c_int), ("stencil_cap", C.c_int), ("total_sites", C.c_int),
                 ("total_cells", C.c_int), ("max_cells_per_axis", C.c_int), ("recheck_gap", C.c_double),
                 ("warps_per_cell", C.c_int), ("active_cells_per_colour", C.c_int), ("launch_mode", C.c_int),
-                ("persistent_blocks", C.c_int)]
+                ("persistent_blocks", C.c_int), ("recompute_every", C.c_int)]
 
 
 LOG_DTYPE = np.dtype([("site", "<i4"), ("move", "<i2"), ("flags", "<i2"), ("status", "<i4"), ("accepted", "<i4"),
@@ -123,6 +125,7 @@ def load():
         "mc_md_state": ([vp, vp, vp], i32),
         "mc_last_error": ([], C.c_char_p),
         "mc_energy_noalloc": ([dbl, i32, vp, vp, vp, vp, vp], i32),
+        "mc_test_fail_alloc": ([i32], None),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -158,12 +161,14 @@ def make_mix(mix):
 
 
 def make_options(precision="fp32", n_cells=0, device=0, stencil_cap=0, recheck_gap=0.0, warps_per_cell=0,
-                 launch_mode=0):
+                 launch_mode=0, recompute_every=0, wait_limit_log2=0):
     o = mc_options()
     o.precision = PREC[precision] if isinstance(precision, str) else int(precision)
     o.n_cells, o.device, o.stencil_cap, o.recheck_gap = int(n_cells), int(device), int(stencil_cap), float(recheck_gap)
     o.warps_per_cell = int(warps_per_cell)
     o.launch_mode = int(launch_mode)
+    o.recompute_every = int(recompute_every)
+    o.wait_limit_log2 = int(wait_limit_log2)
     return o
 
 
@@ -444,18 +449,26 @@ def mc_energy_noalloc(L, n_mol, dev_q_ptr, dev_types_ptr, pot, dev_out_ptr, stre
                                     C.byref(p), C.c_void_p(dev_out_ptr), C.c_void_p(stream_ptr))
 
 
+def mc_test_fail_alloc(after):
+    """Make the device allocation number `after` of the next handle creation
+    fail (test hook of the library's failure paths; < 0 disarms)."""
+    load().mc_test_fail_alloc(int(after))
+
+
 def stats_dict(s):
     return {"attempts": list(s.attempts), "accepts": list(s.accepts), "rejected_geometry": s.rejected_geometry,
             "rejected_bond": s.rejected_bond, "pair_evals": s.pair_evals, "fp64_rechecks": s.fp64_rechecks,
-            "pair_interactions": s.pair_interactions, "sweeps": s.sweeps, "e_run": s.e_run}
+            "pair_interactions": s.pair_interactions, "sweeps": s.sweeps, "e_run": s.e_run,
+            "recomputes": s.recomputes, "drift_last": s.drift_last, "drift_max": s.drift_max}
 
 
 class Handle:
     """One handle of the library (a batch of replicas; one replica by default)."""
 
     def __init__(self, L, xyz, types, pot, precision="fp32", n_cells=0, device=0, stencil_cap=0, recheck_gap=0.0,
-                 n_mol=None, warps_per_cell=0, launch_mode=0):
-        opts = make_options(precision, n_cells, device, stencil_cap, recheck_gap, warps_per_cell, launch_mode)
+                 n_mol=None, warps_per_cell=0, launch_mode=0, recompute_every=0, wait_limit_log2=0):
+        opts = make_options(precision, n_cells, device, stencil_cap, recheck_gap, warps_per_cell, launch_mode,
+                            recompute_every, wait_limit_log2)
         if np.ndim(L) == 0:
             self.h = mc_create(L, xyz, types, pot, opts)
         else:
@@ -580,6 +593,9 @@ class Handle:
 
     def stats(self):
         return mc_state_stats(self.h, self.n_rep)
+
+    def reset_stats(self):
+        mc_reset_stats(self.h)
 
     def set_stream(self, stream_ptr):
         mc_set_stream(self.h, stream_ptr)
