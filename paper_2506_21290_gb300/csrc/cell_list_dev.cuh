@@ -30,10 +30,6 @@ __device__ __forceinline__ void cl_count_item(const DevState &d, int buf, int g,
     d.slot_of[g] = atomicAdd(counts + c, 1);
 }
 
-__device__ __forceinline__ void cl_scatter_item(const DevState &d, int buf_in, int buf_out, int g)
-{
-    d.rec[buf_out][d.cell_start[d.cell_of[g]] + d.slot_of[g]] = d.rec[buf_in][g];
-}
 
 // The random draws and the Metropolis threshold of every attempt of the sweep.
 // Attempt a of cell c (a < occupancy n) is slot start(c) + a; its words are
@@ -82,20 +78,31 @@ __device__ __forceinline__ void attempt_randoms(const DevState &d, int r, int ce
     }
 }
 
+// Scatter atom g into its cell's segment at its counting slot a, and draw the
+// random numbers of attempt a of that cell (when the sweep needs them): the
+// cell's atoms and its attempts are both numbered 0..n-1, so one thread per
+// atom covers every attempt, and the draws depend on (seed, sweep, cell, a,
+// n) only, not on which atom took slot a.
+__device__ __forceinline__ void cl_scatter_item(const DevState &d, int buf_in, int buf_out, int g)
+{
+    const int c = d.cell_of[g];
+    const int start = d.cell_start[c];
+    const int a = d.slot_of[g];
+    d.rec[buf_out][start + a] = d.rec[buf_in][g];
+    if (d.att_rnd != nullptr) {
+        const int r = d.rep_of_site[g];
+        attempt_randoms(d, r, c - d.rep[r].cell_off, start + a, a, d.cell_start[c + 1] - start);
+    }
+}
+
 // Order the atoms of cell c by site index (the record word orders by
 // molecule, then slot), so the layout after a build does not depend on the
-// order in which the atomic counts were taken; then draw the random numbers of
-// the cell's attempts (when the sweep needs them).  One warp.
+// order in which the atomic counts were taken.  One warp.
 __device__ __forceinline__ void cl_order_cell(const DevState &d, int buf, int c, int lane)
 {
     const int start = d.cell_start[c];
     const int n = d.cell_start[c + 1] - start;
     int4 *seg = d.rec[buf] + start;
-    if (d.att_rnd != nullptr && n > 0) {
-        const int r = d.rep_of_site[start];
-        const int cellL = c - d.rep[r].cell_off;
-        for (int a = lane; a < n; a += 32) attempt_randoms(d, r, cellL, start + a, a, n);
-    }
     if (n <= 1) return;
     if (n <= 32) {
         int4 mine = lane < n ? seg[lane] : make_int4(0, 0, 0, 0x7fffffff);
