@@ -6,57 +6,120 @@
 
 namespace flipmc {
 
-// Energy (VIRIAL = false) or pair virial (VIRIAL = true) of every atom i with
-// its partners j > i (site index) in the 27 (or 8) neighbour cells; pairs
-// beyond every cutoff are screened in FP32 and add 0.
+// Energy (VIRIAL = false) or pair virial (VIRIAL = true), one warp per cell:
+// every pair (i, j) with i an atom of the cell and j an atom of the 27 (or,
+// for n_c = 2, the 8) neighbour cells with a larger site index.  Lane k walks
+// neighbour cell k; pairs of different molecules beyond every cutoff (FP32
+// screen with a 1% margin) add exactly 0 and are dropped; the others are
+// gathered in order into a ring and evaluated in FP64 32 at a time, one per
+// lane, so the FP64 pipe works on full warps.  Each lane sums its pairs in
+// gathering order and a fixed butterfly adds the lanes: the cell's sum is the
+// same on every run for a given state.
+constexpr int kCellWarps = 8;       // cells per block
+constexpr int kRing = 64;           // gathered pairs per warp (at most 63 waiting)
+
 template <bool VIRIAL>
-__global__ void pair_sites_kernel(DevState d, int buf, double *e_site)
+__global__ void __launch_bounds__(32 * kCellWarps) pair_cells_kernel(DevState d, int buf, double *e_cell)
 {
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= d.n_sites) return;
-    const int r = d.rep_of_site[g];
-    const RepInfo ri = d.rep[r];
-    const ModelDev &md = *d.model;
-    const int4 me = d.rec[buf][g];
-    const int si = rec_site(me.w), ti = rec_type(me.w), mi = rec_mol(me.w);
-    const int nc = ri.nc;
-    const uint32_t *shift = d.ctr[r].shift;
-    const int cx = (int)cell_axis((uint32_t)me.x, shift[0], nc);
-    const int cy = (int)cell_axis((uint32_t)me.y, shift[1], nc);
-    const int cz = (int)cell_axis((uint32_t)me.z, shift[2], nc);
-    float rc2max = 0.f;
-    for (int k = 0; k < 9; ++k) rc2max = fmaxf(rc2max, md.rc2f[k]);
-    const float pre = rc2max * 1.01f;
-    const bool small = nc == 2;
-    const int ns = small ? 8 : 27;
-    double e = 0.0;
-    for (int k = 0; k < ns; ++k) {
-        int ox, oy, oz;
-        if (small) {
-            ox = k & 1; oy = (k >> 1) & 1; oz = k >> 2;
-        } else {
-            ox = k % 3 - 1; oy = (k / 3) % 3 - 1; oz = k / 9 - 1;
+    __shared__ int2 ring_all[kCellWarps][kRing];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int c = blockIdx.x * kCellWarps + wib;
+    if (c >= d.n_cells) return;   // the whole warp
+    int2 *ring = ring_all[wib];
+    const int s0 = d.cell_start[c];
+    const int n = d.cell_start[c + 1] - s0;
+    double acc = 0.0;
+    if (n > 0) {
+        const int r = d.rep_of_site[s0];
+        const RepInfo ri = d.rep[r];
+        const ModelDev &md = *d.model;
+        const int4 *rec = d.rec[buf];
+        const int nc = ri.nc, cl = c - ri.cell_off;
+        const int cx = cl % nc, cy = (cl / nc) % nc, cz = cl / (nc * nc);
+        const bool small = nc == 2;
+        const int ns = small ? 8 : 27;
+        int cst = 0, cnt = 0;
+        if (lane < ns) {
+            int ox, oy, oz;
+            if (small) {
+                ox = lane & 1; oy = (lane >> 1) & 1; oz = lane >> 2;
+            } else {
+                ox = lane % 3 - 1; oy = (lane / 3) % 3 - 1; oz = lane / 9 - 1;
+            }
+            const int nb = ri.cell_off + (((cz + oz + nc) % nc) * nc + (cy + oy + nc) % nc) * nc + (cx + ox + nc) % nc;
+            cst = d.cell_start[nb];
+            cnt = d.cell_start[nb + 1] - cst;
         }
-        const int c = ri.cell_off + (((cz + oz + nc) % nc) * nc + (cy + oy + nc) % nc) * nc + (cx + ox + nc) % nc;
-        const int s0 = d.cell_start[c], s1 = d.cell_start[c + 1];
-        for (int j = s0; j < s1; ++j) {
-            const int4 o = d.rec[buf][j];
-            const int sj = rec_site(o.w);
-            if (sj <= si) continue;
+        const int maxc = __reduce_max_sync(0xffffffffu, cnt);
+        float rc2max = 0.f;
+        for (int k = 0; k < 9; ++k) rc2max = fmaxf(rc2max, md.rc2f[k]);
+        const float pre = rc2max * 1.01f;
+        const unsigned lt = (1u << lane) - 1u;
+        int head = 0, tail = 0;   // warp-uniform
+        auto eval = [&](int e) {
+            const int2 p = ring[e & (kRing - 1)];
+            const int4 me = rec[s0 + p.x], o = rec[p.y];
             const int dx = (int)((uint32_t)o.x - (uint32_t)me.x);
             const int dy = (int)((uint32_t)o.y - (uint32_t)me.y);
             const int dz = (int)((uint32_t)o.z - (uint32_t)me.z);
-            const bool bonded = rec_mol(o.w) == mi;
-            if (!bonded) {
-                const float fx = (float)dx * ri.hf, fy = (float)dy * ri.hf, fz = (float)dz * ri.hf;
-                if (fx * fx + fy * fy + fz * fz > pre) continue;
-            }
             const double r2 = r2_fixed64(dx, dy, dz, ri.h);
-            const int ab = 3 * ti + rec_type(o.w);
-            e = __dadd_rn(e, VIRIAL ? virial64(md, r2, ab, bonded) : phi64(md, r2, ab, bonded));
+            const bool bonded = rec_mol(o.w) == rec_mol(me.w);
+            const int ab = 3 * rec_type(me.w) + rec_type(o.w);
+            acc = __dadd_rn(acc, VIRIAL ? virial64(md, r2, ab, bonded) : phi64(md, r2, ab, bonded));
+        };
+        for (int i = 0; i < n; ++i) {
+            const int4 me = rec[s0 + i];
+            const int si = rec_site(me.w), mi = rec_mol(me.w);
+            for (int k = 0; k < maxc; ++k) {
+                bool hit = false;
+                if (k < cnt) {
+                    const int4 o = rec[cst + k];
+                    if (rec_site(o.w) > si) {
+                        if (rec_mol(o.w) == mi) {
+                            hit = true;
+                        } else {
+                            const float fx = (float)(int)((uint32_t)o.x - (uint32_t)me.x) * ri.hf;
+                            const float fy = (float)(int)((uint32_t)o.y - (uint32_t)me.y) * ri.hf;
+                            const float fz = (float)(int)((uint32_t)o.z - (uint32_t)me.z) * ri.hf;
+                            hit = fx * fx + fy * fy + fz * fz <= pre;
+                        }
+                    }
+                }
+                const unsigned b = __ballot_sync(0xffffffffu, hit);
+                if (hit) ring[(tail + __popc(b & lt)) & (kRing - 1)] = make_int2(i, cst + k);
+                tail += __popc(b);
+                if (tail - head >= 32) {
+                    __syncwarp();
+                    eval(head + lane);
+                    head += 32;
+                    __syncwarp();
+                }
+            }
         }
+        __syncwarp();
+        if (lane < tail - head) eval(head + lane);
     }
-    e_site[ri.site_off + si] = e;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc = __dadd_rn(acc, __shfl_xor_sync(0xffffffffu, acc, o));
+    if (lane == 0) e_cell[c] = acc;
+}
+
+// Fixed-order sum of the per-cell values of each replica (one block each).
+__global__ void __launch_bounds__(256) replica_cells_sum_kernel(DevState d, const double *v, double *out)
+{
+    const int r = blockIdx.x;
+    const RepInfo ri = d.rep[r];
+    const int n = ri.nc * ri.nc * ri.nc;
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += 256) s = __dadd_rn(s, v[ri.cell_off + i]);
+    __shared__ double red[256];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] = __dadd_rn(red[threadIdx.x], red[threadIdx.x + w]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[r] = red[0];
 }
 
 // Fixed-order sum of a per-site (or per-molecule) array over each replica.
@@ -79,10 +142,10 @@ __global__ void __launch_bounds__(256) replica_sum_kernel(DevState d, const doub
     if (threadIdx.x == 0) out[(size_t)r * stride + offset] = scale_inv_n != 0.0 ? red[0] / (double)n : red[0];
 }
 
-void launch_energy(const DevState &d, int buf, double *e_site, double *e_out_dev, cudaStream_t st)
+void launch_energy(const DevState &d, int buf, double *e_cell, double *e_out_dev, cudaStream_t st)
 {
-    pair_sites_kernel<false><<<(d.n_sites + 255) / 256, 256, 0, st>>>(d, buf, e_site);
-    replica_sum_kernel<<<d.n_rep, 256, 0, st>>>(d, e_site, 0, 0.0, e_out_dev, 1, 0);
+    pair_cells_kernel<false><<<(d.n_cells + kCellWarps - 1) / kCellWarps, 32 * kCellWarps, 0, st>>>(d, buf, e_cell);
+    replica_cells_sum_kernel<<<d.n_rep, 256, 0, st>>>(d, e_cell, e_out_dev);
 }
 
 // Drift check of the running total against a fresh FP64 recompute E, per
@@ -106,10 +169,10 @@ void launch_drift(const DevState &d, const double *E, double *drift, cudaStream_
     drift_kernel<<<(d.n_rep + 127) / 128, 128, 0, st>>>(d, E, drift);
 }
 
-void launch_virial(const DevState &d, int buf, double *w_site, double *w_out_dev, cudaStream_t st)
+void launch_virial(const DevState &d, int buf, double *w_cell, double *w_out_dev, cudaStream_t st)
 {
-    pair_sites_kernel<true><<<(d.n_sites + 255) / 256, 256, 0, st>>>(d, buf, w_site);
-    replica_sum_kernel<<<d.n_rep, 256, 0, st>>>(d, w_site, 0, 0.0, w_out_dev, 1, 0);
+    pair_cells_kernel<true><<<(d.n_cells + kCellWarps - 1) / kCellWarps, 32 * kCellWarps, 0, st>>>(d, buf, w_cell);
+    replica_cells_sum_kernel<<<d.n_rep, 256, 0, st>>>(d, w_cell, w_out_dev);
 }
 
 // Unwrapped fixed-point positions and types in site-index order.

@@ -14,8 +14,8 @@ struct ObsState {
     double *u0;      // 3 per molecule: unit orientation at t0
 };
 
-// FP64 energy per replica into e_out_dev[n_rep]; e_site is n_sites scratch.
-void launch_energy(const DevState &d, int buf, double *e_site, double *e_out_dev, cudaStream_t st);
+// FP64 energy per replica into e_out_dev[n_rep]; e_cell is n_cells scratch.
+void launch_energy(const DevState &d, int buf, double *e_cell, double *e_out_dev, cudaStream_t st);
 // Periodic drift check: drift[2r] = |e_run - E| / |E| (last), drift[2r+1] its
 // largest value; one recompute counted; e_run restarts from E[r].
 void launch_drift(const DevState &d, const double *E, double *drift, cudaStream_t st);
@@ -25,7 +25,7 @@ void launch_sq(const DevState &d, const long long *X, const double *qv, int n_q,
 void launch_pair_hist(const DevState &d, const long long *X, int max_sites, double dr, int n_bins,
                       unsigned long long *counts, cudaStream_t st);
 // FP64 pair virial sum W = sum_{i<j} -r dphi/dr per replica into w_out_dev[n_rep].
-void launch_virial(const DevState &d, int buf, double *w_site, double *w_out_dev, cudaStream_t st);
+void launch_virial(const DevState &d, int buf, double *w_cell, double *w_out_dev, cudaStream_t st);
 // unwrapped positions (3 per site) and types in site order
 void launch_gather(const DevState &d, int buf, long long *X, int *types, cudaStream_t st);
 void launch_set_t0(const DevState &d, const long long *X, const int *types, const ObsState &o, cudaStream_t st);

@@ -122,7 +122,7 @@ struct mc_handle {
     MixDev *d_mix = nullptr;
     int *d_rep_of_site = nullptr;
     int *d_act_off = nullptr;
-    double *d_e_site = nullptr;
+    double *d_e_site = nullptr;          // per-cell (or per-site) FP64 partial sums
     double *d_e_out = nullptr;
     long long *d_X = nullptr;
     int *d_types = nullptr;
@@ -559,7 +559,7 @@ int create_impl(mc_handle **out, int n_rep, const double *L, const int32_t *n_mo
         (rc = h->alloc(&cs, h->n_cells + 1)) || (rc = h->alloc(&co, h->n_sites)) || (rc = h->alloc(&so, h->n_sites)) ||
         (rc = h->alloc(&img, 3 * (size_t)h->n_sites)) || (rc = h->alloc(&cde, h->n_cells)) ||
         (rc = h->alloc(&stats, (size_t)STAT_N * n_rep)) || (rc = h->alloc(&erun, n_rep)) ||
-        (rc = h->alloc(&err, 1)) || (rc = h->alloc(&h->d_e_site, h->n_sites)) ||
+        (rc = h->alloc(&err, 1)) || (rc = h->alloc(&h->d_e_site, std::max(h->n_sites, h->n_cells))) ||
         (rc = h->alloc(&h->d_e_out, n_rep)) || (rc = h->alloc(&h->d_X, 3 * (size_t)h->n_sites)) ||
         (rc = h->alloc(&h->d_types, h->n_sites)) || (rc = h->alloc(&h->obs.X0, 3 * (size_t)h->n_sites)) ||
         (rc = h->alloc(&h->obs.kref, M_tot)) || (rc = h->alloc(&h->obs.u0, 3 * (size_t)M_tot)) ||

@@ -57,6 +57,7 @@ constexpr size_t kOffCellOf = al256(kOffStart + sizeof(int) * (kMaxCells + 1));
 constexpr size_t kOffSlotOf = al256(kOffCellOf + sizeof(int) * kMaxSites);
 constexpr size_t kOffESite = al256(kOffSlotOf + sizeof(int) * kMaxSites);
 constexpr size_t kScratchBytes = al256(kOffESite + sizeof(double) * kMaxSites);
+static_assert(kMaxCells <= kMaxSites, "the partial-sum region holds one double per cell");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
@@ -221,7 +222,7 @@ extern "C" int mc_energy_noalloc(double L, int n_mol, const uint32_t *dev_q, con
     d.cell_start = (int *)(base + kOffStart);
     d.cell_of = (int *)(base + kOffCellOf);
     d.slot_of = (int *)(base + kOffSlotOf);
-    double *e_site = (double *)(base + kOffESite);
+    double *e_part = (double *)(base + kOffESite);   // per-cell partial sums
 
     cudaError_t e = cudaSuccess;
     auto chk = [&](cudaError_t x) {
@@ -233,7 +234,7 @@ extern "C" int mc_energy_noalloc(double L, int n_mol, const uint32_t *dev_q, con
     chk(cudaGetLastError());
     launch_cell_list(d, 0, 1, st);
     chk(cudaGetLastError());
-    launch_energy(d, 1, e_site, dev_E_out, st);
+    launch_energy(d, 1, e_part, dev_E_out, st);
     chk(cudaGetLastError());
     noalloc_poison_kernel<<<1, 32, 0, st>>>(d.err, dev_E_out);
     chk(cudaGetLastError());
