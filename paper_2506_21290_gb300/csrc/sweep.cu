@@ -1185,12 +1185,12 @@ __device__ void run_cell(const DevState &d, int buf, int colour, const LogArgs &
     const WarpScr S = warp_scr(G, wig);
 
     // ---- which cell ----
-    const int r = find_segment(d.act_off, d.n_rep, g);
+    const int r = d.n_rep == 1 ? 0 : d.rep_of_act[g];
     const RepInfo ri = d.rep[r];
     const RepParam dy = d.par[r];
     const RepCtr ct = d.ctr[r];
     const int nc = ri.nc, h2 = nc >> 1;
-    const int a_loc = g - d.act_off[r];
+    const int a_loc = g - ri.act_off;
     const int cx = 2 * (a_loc % h2) + (colour & 1);
     const int cy = 2 * ((a_loc / h2) % h2) + ((colour >> 1) & 1);
     const int cz = 2 * (a_loc / (h2 * h2)) + ((colour >> 2) & 1);
