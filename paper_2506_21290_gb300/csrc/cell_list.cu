@@ -68,12 +68,12 @@ __global__ void cl_scatter_kernel(DevState d, int buf_in, int buf_out)
     if (g < d.n_sites) cl_scatter_item(d, buf_in, buf_out, g);
 }
 
-// One warp per cell.
+// One warp per four cells.
 __global__ void cl_order_kernel(DevState d, int buf)
 {
     const int lane = threadIdx.x & 31;
-    const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (c < d.n_cells) cl_order_cell(d, buf, c, lane);
+    const int c = 4 * (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5));
+    if (c < d.n_cells) cl_order_cells4(d, buf, c, lane);
 }
 
 void launch_cell_list(const DevState &d, int buf_in, int buf_out, cudaStream_t st)
@@ -85,7 +85,7 @@ void launch_cell_list(const DevState &d, int buf_in, int buf_out, cudaStream_t s
     cl_scan_kernel<<<1, 1024, 0, st>>>(d);
     cl_scatter_kernel<<<nb, tb, 0, st>>>(d, buf_in, buf_out);
     const int wpb = 8;
-    cl_order_kernel<<<(d.n_cells + wpb - 1) / wpb, 32 * wpb, 0, st>>>(d, buf_out);
+    cl_order_kernel<<<(d.n_cells + 4 * wpb - 1) / (4 * wpb), 32 * wpb, 0, st>>>(d, buf_out);
 }
 
 }  // namespace flipmc

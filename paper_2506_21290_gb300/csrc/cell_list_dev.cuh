@@ -132,4 +132,33 @@ __device__ __forceinline__ void cl_order_cell(const DevState &d, int buf, int c,
     __syncwarp();
 }
 
+// Order the four cells c0 .. c0 + 3 at once, eight lanes each, when they hold
+// at most eight atoms (the usual case at the paper's density); a larger cell
+// is then ordered by the whole warp.  One warp.
+__device__ __forceinline__ void cl_order_cells4(const DevState &d, int buf, int c0, int lane)
+{
+    const int sub = lane & 7, c = c0 + (lane >> 3);
+    int start = 0, n = 0;
+    if (c < d.n_cells) {
+        start = d.cell_start[c];
+        n = d.cell_start[c + 1] - start;
+    }
+    int4 *seg = d.rec[buf] + start;
+    const bool mine_ok = sub < n && n <= 8;
+    const int4 mine = mine_ok ? seg[sub] : make_int4(0, 0, 0, 0x7fffffff);
+    const unsigned key = (unsigned)mine.w;
+    int rank = 0;
+#pragma unroll
+    for (int m = 0; m < 8; ++m) rank += __shfl_sync(0xffffffffu, key, m, 8) < key;
+    __syncwarp();
+    if (mine_ok && n > 1) seg[rank] = mine;
+    __syncwarp();
+    unsigned big = __ballot_sync(0xffffffffu, sub == 0 && n > 8);
+    while (big) {
+        const int k = __ffs(big) - 1;
+        big &= big - 1;
+        cl_order_cell(d, buf, c0 + (k >> 3), lane);
+    }
+}
+
 }  // namespace flipmc
