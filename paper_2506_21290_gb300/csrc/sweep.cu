@@ -140,6 +140,49 @@ struct PosH {
 // shared memory
 // ---------------------------------------------------------------------------
 
+// ---------------------------------------------------------------------------
+// Bulk copies global -> shared (cp.async.bulk) completing on an mbarrier: the
+// staging of one-warp groups (W = 1)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *mb)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n\tfence.proxy.async.shared::cta;" ::"r"(smem_u32(mb))
+                 : "memory");
+}
+
+// the one arrival of a phase, announcing the bytes its copies will deliver
+__device__ __forceinline__ void mbar_arrive_expect(uint64_t *mb, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mb)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_done(uint64_t *mb, unsigned parity)
+{
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok)
+                 : "r"(smem_u32(mb)), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+
+// bytes (a multiple of 16, both addresses 16-byte aligned) from global to
+// shared.  The proxy fence orders this group's earlier generic accesses to the
+// destination before the copy's writes; the source was written before the
+// last grid-wide barrier (or kernel boundary), or by a neighbour cell whose
+// release the group acquired, and the copy reads it in L2.
+__device__ __forceinline__ void bulk_to_smem(void *dst, const void *src, unsigned bytes, uint64_t *mb)
+{
+    asm volatile("fence.proxy.async.shared::cta;\n\t"
+                 "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(mb))
+                 : "memory");
+}
+
 // per warp: interaction queue, and (aliased, used after it) the FP64 term buffers
 struct WarpScr {
     int *qc;                    // [QW + 1] queued candidate indices, then a slot that takes discarded writes
@@ -180,6 +223,7 @@ struct Group {
     int4 *rec;                  // [cap] raw records {qx, qy, qz, w} of the neighbourhood, own cell first,
                                 //       then kPadSlots padding records
     int4 *orig;                 // [own_cap] the own cell as staged (periodic images at write-back)
+    uint64_t *mbar;             // completion barrier of the bulk copies that stage rec (W = 1)
     uint32_t *rnd;              // [32 * 8] random words of a chunk of attempts
     double *thr64;              // [32]
     float *thr32;               // [32]
@@ -191,7 +235,7 @@ struct Group {
     unsigned char *warp_base;   // W per-warp scratch blocks
 };
 
-enum { MS_K = 0, MS_N = 1, MS_START = 2, MS_CLASH = 4 /* [W <= 8] */ };
+enum { MS_K = 0, MS_N = 1, MS_START = 2, MS_PHASE = 3, MS_CLASH = 4 /* [W <= 8] */, MS_FAIL = 16 };
 
 __host__ __device__ constexpr size_t al16(size_t x) { return (x + 15) & ~size_t(15); }
 
@@ -204,7 +248,7 @@ __host__ __device__ inline size_t warp_scr_bytes()
 
 __host__ __device__ inline size_t group_bytes(int cap, int own_cap, int W)
 {
-    return al16(sizeof(int4) * cap) + al16(sizeof(int4) * own_cap) +
+    return al16(sizeof(int4) * cap) + al16(sizeof(int4) * own_cap) + 16 +
            al16(sizeof(uint32_t) * 256) +
            al16(sizeof(double) * 32) + al16(sizeof(float) * 32) + 3 * al16(sizeof(int) * 32) +
            al16(sizeof(Near) * W) + al16(sizeof(Tally) * W) + (size_t)W * warp_scr_bytes();
@@ -221,6 +265,7 @@ __device__ inline Group carve(unsigned char *base, int cap, int own_cap, int W)
     };
     s.rec = (int4 *)take(sizeof(int4) * cap);
     s.orig = (int4 *)take(sizeof(int4) * own_cap);
+    s.mbar = (uint64_t *)take(16);
     s.rnd = (uint32_t *)take(sizeof(uint32_t) * 256);
     s.thr64 = (double *)take(sizeof(double) * 32);
     s.thr32 = (float *)take(sizeof(float) * 32);
@@ -1138,6 +1183,17 @@ __device__ __forceinline__ void load_tables(const DevState &d, ModelDev &md, Mix
     for (int i = threadIdx.x; i < (int)(sizeof(MixDev) / 4); i += blockDim.x) dst2[i] = src2[i];
 }
 
+// Once per launch, by the first thread of each group: the bulk-copy barrier
+// and its phase parity (the caller synchronises the block afterwards).
+__device__ __forceinline__ void init_group(unsigned char *gsmem, const DevState &d, int W)
+{
+    if (threadIdx.x % (32 * W) == 0) {
+        const Group G = carve(gsmem, d.stencil_cap, d.own_cap, W);
+        mbar_init(G.mbar);
+        G.misc[MS_PHASE] = 0;
+    }
+}
+
 // Ordering of the colour phases inside one persistent launch, cell by cell:
 // a cell may start its phase of sweep s once every neighbour cell of a smaller
 // colour has finished its phase of sweep s (the neighbours' writes are then
@@ -1250,6 +1306,18 @@ __device__ void run_cell(const DevState &d, int buf, int colour, const LogArgs &
         if (lane == 0) {
             G.misc[MS_N] = cnt;
             G.misc[MS_START] = cst;
+            G.misc[MS_FAIL] = 0;
+        }
+        if constexpr (W == 1) {
+            // one-warp groups stage by bulk copies, one per cell, all
+            // completing on the group's barrier (only when they fit)
+            const int Kw = __shfl_sync(FULL, incl, 31), nw0 = __shfl_sync(FULL, cnt, 0);
+            if (Kw + PADS <= cap && nw0 <= own_cap) {
+                if (lane == 0) mbar_arrive_expect(G.mbar, 16u * (unsigned)Kw);
+                __syncwarp();
+                if (lane < ns && cnt > 0)
+                    bulk_to_smem(G.rec + (incl - cnt), d.rec[buf] + cst, 16u * (unsigned)cnt, G.mbar);
+            }
         }
     }
     gsync<W>(gid);
@@ -1265,15 +1333,49 @@ __device__ void run_cell(const DevState &d, int buf, int colour, const LogArgs &
         return;
     }
 
-    // ---- stage: the raw records of the neighbourhood, loaded straight from
-    // L2 (the waits above acquired the neighbours' writes; .cg loads bypass
-    // L1, which may hold lines of an earlier phase).  Lane j of every warp
-    // takes cell j, warp w its records w, w + W, ..., SU loads in flight;
-    // the own cell (j = 0) is also kept as staged.  Warp 0 stores the first 32
-    // attempts' draws; padding records follow the K atoms (no molecule, never
-    // within reach: the screens and the interaction passes read them instead
-    // of branching) ----
-    {
+    if constexpr (W == 1) {
+        // ---- stage (one warp): wait for the bulk copies (bounded), keep a copy
+        // of the own cell, store the first 32 attempts' draws; padding records
+        // follow the K atoms (no molecule, never within reach: the screens and
+        // the interaction passes read them instead of branching) ----
+        const unsigned parity = (unsigned)G.misc[MS_PHASE];
+        unsigned spins = 0;
+        bool ok = true;
+        while (!mbar_done(G.mbar, parity)) {
+            if (++spins > (1u << 22)) {
+                ok = false;
+                break;
+            }
+        }
+        if (!ok) G.misc[MS_FAIL] = 1;
+        for (int idx = lane; ok && idx < n; idx += 32) G.orig[idx] = G.rec[idx];   // the own cell as staged
+        if (lane < n) {
+            uint4 *wv = (uint4 *)(G.rnd + 8 * lane);
+            wv[0] = rb0;
+            wv[1] = rb1;
+            if (PREC == MC_PREC_FP64) G.thr64[lane] = th64;
+            else G.thr32[lane] = th32;
+        }
+        if (lane < PADS) G.rec[K + lane] = make_int4(0, 0, 0, PAD_W);
+        __syncwarp();
+        if (G.misc[MS_FAIL]) {
+            // copies that never completed: record it, give them one more bounded
+            // wait, and leave the cell untouched
+            if (lane == 0) atomicOr(d.err, ERR_TIMEOUT);
+            for (unsigned t2 = 0; t2 < (1u << 22) && !mbar_done(G.mbar, parity); ++t2) {
+            }
+            if (lane == 0 && dep != 0) signal_done(d.cell_done + cellG);
+            return;
+        }
+        if (lane == 0) G.misc[MS_PHASE] = (int)(parity ^ 1u);   // the warp has read the parity
+    } else {
+        // ---- stage (W >= 2 warps): the raw records of the neighbourhood,
+        // loaded straight from L2 (the waits above acquired the neighbours'
+        // writes; .cg loads bypass L1, which may hold lines of an earlier
+        // phase).  Lane j of every warp takes cell j, warp w its records w,
+        // w + W, ..., SU loads in flight; the own cell (j = 0) is also kept as
+        // staged.  Warp 0 stores the first 32 attempts' draws; padding records
+        // follow the K atoms ----
         if (lane < ns) {
             const int off = G.coff[lane], cnt = G.coff[lane + 1] - off;
             const int4 *src = d.rec[buf] + G.cstart[lane];
@@ -1300,8 +1402,8 @@ __device__ void run_cell(const DevState &d, int buf, int colour, const LogArgs &
             else G.thr32[lane] = th32;
         }
         if (gt < PADS) G.rec[K + gt] = make_int4(0, 0, 0, PAD_W);
+        gsync<W>(gid);
     }
-    gsync<W>(gid);
 
     CellCtx c;
     c.md = &md;
@@ -1465,6 +1567,7 @@ __global__ void __launch_bounds__(block_threads<W>(), W == 1 ? 3 : 1) phase_kern
     __shared__ MixDev mx;
     const int gid = threadIdx.x / (32 * W);
     unsigned char *gsmem = smem + (size_t)gid * group_bytes(d.stencil_cap, d.own_cap, W);
+    init_group(gsmem, d, W);
     load_tables(d, md, mx);
     __syncthreads();
     const int g = blockIdx.x * CPB + gid;
@@ -1592,6 +1695,7 @@ __global__ void __launch_bounds__(block_threads<W>(), W == 1 ? 3 : 1) sweep_pers
     __shared__ int tmp[NT / 32];
     const int gid = threadIdx.x / T;
     unsigned char *gsmem = smem + (size_t)gid * group_bytes(d.stencil_cap, d.own_cap, W);
+    init_group(gsmem, d, W);
     load_tables(d, md, mx);
     __syncthreads();
     const int nthr = gridDim.x * NT;
