@@ -229,6 +229,10 @@ def cpu_baseline(wl, name, budget_s, T, mix):
                       % (n, M0, name), "cpu_model": _cpu_model()}
 
 
+# Arm CPU part numbers of /proc/cpuinfo (Arm's published MIDR values)
+ARM_PARTS = {"0xd0c": "Neoverse-N1", "0xd40": "Neoverse-V1", "0xd49": "Neoverse-N2", "0xd4f": "Neoverse-V2"}
+
+
 def _cpu_model():
     try:
         with open("/proc/cpuinfo") as f:
@@ -236,7 +240,8 @@ def _cpu_model():
         for key in ("model name", "CPU part"):
             for line in txt.splitlines():
                 if line.startswith(key):
-                    return line.split(":", 1)[1].strip() + " (%s)" % os.uname().machine
+                    v = line.split(":", 1)[1].strip()
+                    return "%s (%s)" % (ARM_PARTS.get(v, v), os.uname().machine)
     except OSError:
         pass
     return os.uname().machine

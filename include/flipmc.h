@@ -170,6 +170,7 @@ typedef struct {
     int launch_mode;          /* 1: a CUDA graph per sweep; 2: one persistent launch per call */
     int persistent_blocks;    /* blocks of the persistent launch (0 with graphs) */
     int recompute_every;      /* as in mc_options */
+    int binary_version;       /* compute capability the sweep kernels were built for (103 = sm_103) */
 } mc_info;
 
 /* One attempted move as recorded by mc_sweep_logged(). */

@@ -38,6 +38,10 @@ int persistent_grid(const DevState &d, int warps_per_cell, int max_blocks);
 int launch_persistent(const DevState &d, int buf, int n_sweeps, int warps_per_cell, int grid, unsigned int *bar,
                       int *scan_tot, cudaStream_t st);
 
+// compute capability the sweep kernels were built for (cudaFuncAttributes
+// binaryVersion, e.g. 103), or -1
+int sweep_binary_version();
+
 // the calling thread's last error, as mc_last_error() reports it; returns code
 int record_error(int code, const char *msg);
 

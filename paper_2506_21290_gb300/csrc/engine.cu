@@ -1760,6 +1760,7 @@ int mc_get_info(mc_handle *h, mc_info *info)
     info->launch_mode = h->pgrid > 0 ? 2 : 1;
     info->persistent_blocks = h->pgrid;
     info->recompute_every = h->recompute_every;
+    info->binary_version = sweep_binary_version();
     return MC_OK;
 }
 

@@ -1784,6 +1784,13 @@ __global__ void __launch_bounds__(block_threads<W>(), W == 1 ? 3 : 1) sweep_pers
     }
 }
 
+int sweep_binary_version()
+{
+    cudaFuncAttributes a{};
+    if (cudaFuncGetAttributes(&a, finalize_kernel) != cudaSuccess) return -1;
+    return a.binaryVersion;
+}
+
 size_t phase_smem_bytes(int stencil_cap, int own_cap, int warps_per_cell)
 {
     const int nt = warps_per_cell > 4 ? 32 * warps_per_cell : BLOCK;

@@ -64,7 +64,7 @@ class mc_info(C.Structure):
     _fields_ = [("n_rep", C.c_int), ("precision", C.c_int), ("stencil_cap", C.c_int), ("total_sites", C.c_int),
                 ("total_cells", C.c_int), ("max_cells_per_axis", C.c_int), ("recheck_gap", C.c_double),
                 ("warps_per_cell", C.c_int), ("active_cells_per_colour", C.c_int), ("launch_mode", C.c_int),
-                ("persistent_blocks", C.c_int), ("recompute_every", C.c_int)]
+                ("persistent_blocks", C.c_int), ("recompute_every", C.c_int), ("binary_version", C.c_int)]
 
 
 LOG_DTYPE = np.dtype([("site", "<i4"), ("move", "<i2"), ("flags", "<i2"), ("status", "<i4"), ("accepted", "<i4"),

@@ -182,9 +182,10 @@ def test_flip_moves_speed_up_relaxation_more_as_T_drops():
 def test_flip_mc_onset_time_is_the_papers():
     """Sec. III.C: for flip MC, tau_alpha at the onset temperature T_o = 2.1 is
     tau_o = 1.3e3 MC steps.  The paper does not state the atom step size (ours
-    is 0.1, uniform per axis), so the pin allows a factor of 2.  Measured here
-    with 8 replicas: 1637 sweeps at T = 2.0 and 913 at T = 2.5, about 1.46e3
-    at 2.1."""
+    is 0.1, uniform per axis), so the pin allows a factor of 2.  This test
+    measures tau_alpha at T = 2.1 with 4 replicas and prints it; the speedup
+    runs at T = 2.0 (1637 sweeps) and 2.5 (913), 8 replicas each, interpolate
+    to about 1.46e3 there."""
     from paper_2506_21290_gb300 import speedup as SP
     r = SP.measure(2.1, W.PAPER_MIX, 1000, 4, 5000, 5000, 15000, seed=300)
     print("tau_alpha(flip, T = 2.1) = %.0f +- %.0f sweeps" % (r["tau_alpha"], r["tau_alpha_sem"]))

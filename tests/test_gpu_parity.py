@@ -283,6 +283,12 @@ def test_persistent_launch_matches_graphs(precision, wpc, M):
         _compare_state(hp, ch)
 
 
+def test_kernels_are_built_for_sm_103():
+    L, xyz, t = _start(64, 0)
+    h = F.Handle(L, xyz, t, POT)
+    assert h.info["binary_version"] == 103
+
+
 def test_invalid_inputs_are_rejected():
     L, xyz, t = _start(64, 0)
     bad_t = t.copy()
