@@ -76,7 +76,9 @@ def parse():
     return ap.parse_args()
 
 
-DEFAULT_SPS = {"tiny-64": 100, "single-1000": 100, "single-8000": 20, "batched-256": 5, "large-64000": 100}
+# sweeps per step (each step ends with an FP64 energy recompute): 20 for the
+# single-8000 and batched workloads, 100 where the workload names that interval
+DEFAULT_SPS = {"tiny-64": 100, "single-1000": 100, "single-8000": 20, "batched-256": 20, "large-64000": 100}
 
 
 def combine_ranks(ms, attempts, pairs, dist=None, device="cpu"):

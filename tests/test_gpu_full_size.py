@@ -77,3 +77,24 @@ def test_large_64000_properties():
     hs = F.Handle(L, xyz, t, POT, precision="fp32")
     hs.set_state_fixed(q_shift, None, tp)
     assert hs.energy()[0] == pytest.approx(E, rel=1e-12)
+
+
+def test_batched_256_energies_equal_the_oracles_brute_force():
+    """The whole batched workload (256 replicas, 823k atoms), after three FP32
+    sweeps in the launch form the bench times: the per-replica FP64 energies
+    (warp per cell, neighbour cells) against the oracle's brute force over all
+    pairs of the same fixed-point state, for the smallest, the largest and
+    a spread of replicas."""
+    Ms, Ts = W.replica_mix(W.WORKLOADS["batched-256"]["R"], seed=W.WORKLOADS["batched-256"]["seed"])
+    Ls = np.array([W.box_length(int(M)) for M in Ms])
+    starts = [W.lattice_start(int(M), Ls[k], k) for k, M in enumerate(Ms)]
+    h = F.Handle(Ls, np.concatenate([s[0] for s in starts]), np.concatenate([s[1] for s in starts]), POT,
+                 precision="fp32", n_mol=Ms.astype(np.int32), warps_per_cell=1, launch_mode=1)
+    h.sweep(3, Ts, W.PAPER_MIX, np.arange(len(Ms), dtype=np.uint64))
+    E = h.energy()
+    q, X, t = h.state_fixed()
+    offs = np.concatenate([[0], np.cumsum(3 * Ms)])
+    pick = sorted(set([int(np.argmin(Ms)), int(np.argmax(Ms))] + list(range(0, len(Ms), 37))))
+    for k in pick:
+        sl = slice(offs[k], offs[k + 1])
+        assert E[k] == pytest.approx(oracle.energy(float(Ls[k]), q[sl], t[sl], POT), rel=1e-12), k
