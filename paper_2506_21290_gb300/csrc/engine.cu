@@ -571,7 +571,8 @@ int create_impl(mc_handle **out, int n_rep, const double *L, const int32_t *n_mo
         (rc = h->alloc(&h->d_obs_out, 3 * (size_t)n_rep)) ||
         (rc = h->alloc(&h->ds.att_rnd, 2 * (size_t)h->n_sites)) || (rc = h->alloc(&h->d_bar, 2)) ||
         (rc = h->alloc(&h->ds.cell_done, h->n_cells)) || (rc = h->alloc(&h->ds.cell_count2, h->n_cells)) ||
-        (rc = h->alloc(&h->d_scan_tot, kMaxPersistentBlocks)) || (rc = h->alloc(&h->d_drift, 2 * (size_t)n_rep)) ||
+        (rc = h->alloc(&h->d_scan_tot, kMaxPersistentBlocks)) ||
+        (rc = h->alloc(&h->ds.scan_part, (size_t)h->n_cells / 1024 + 2)) || (rc = h->alloc(&h->d_drift, 2 * (size_t)n_rep)) ||
         (rc = h->precision == MC_PREC_FP64 ? h->alloc(&h->ds.att_thr64, h->n_sites)
                                            : h->alloc(&h->ds.att_thr32, h->n_sites))) {
         mc_destroy(h);

@@ -104,6 +104,7 @@ struct DevState {
     int *cell_count;
     int *cell_count2;    // second count buffer (persistent launch: sweep s + 1 is counted while sweep s finishes)
     int *cell_start;     // n_cells + 1
+    int *scan_part;      // ceil(n_cells / 1024) + 1 block totals of the multi-block scan (nullable: one block)
     int *cell_of;
     int *slot_of;
     int *img;            // 3 per site, indexed by global site index
