@@ -487,6 +487,13 @@ int create_impl(mc_handle **out, int n_rep, const double *L, const int32_t *n_mo
         ri.inv_h = kTwo32 / L[r];
         ri.hf = (float)ri.h;
         ri.h2f = (float)(ri.h * ri.h);
+        // the radii of the screens and of the conflict test, in FP32 as the
+        // kernels use them (one rounding per operation)
+        float rc2max = 0.f;
+        for (int k = 0; k < 9; ++k) rc2max = std::fmax(rc2max, h->model_host.rc2f[k]);
+        ri.pre_r2 = rc2max * 1.01f;
+        ri.r2q = ri.pre_r2 / ri.h2f;
+        ri.rconf = rc2max * 1.0201f / ri.h2f;
         h->reps.push_back(ri);
         for (int i = 0; i < ri.n_sites; ++i) rep_of_site.push_back(r);
         sites += ri.n_sites;

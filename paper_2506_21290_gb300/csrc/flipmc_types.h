@@ -36,6 +36,9 @@ struct RepInfo {
     double L, h, inv_h;
     float hf;
     float h2f;       // h^2 rounded to FP32
+    float pre_r2;    // screening radius squared (sigma units): 1.01 x the largest WCA cutoff squared, FP32
+    float r2q;       // the same in fixed-point units squared: pre_r2 / h2f
+    float rconf;     // conflict radius squared, fixed-point units: rc2max x 1.0201 / h2f
 };
 
 // Per-replica parameters of the current sweep call (written by the host).

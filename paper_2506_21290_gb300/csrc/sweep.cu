@@ -1373,19 +1373,20 @@ __device__ void run_cell(const DevState &d, int buf, int colour, const LogArgs &
         // loaded straight from L2 (the waits above acquired the neighbours'
         // writes; .cg loads bypass L1, which may hold lines of an earlier
         // phase).  Lane j of every warp takes cell j, warp w its records w,
-        // w + W, ..., SU loads in flight; the own cell (j = 0) is also kept as
+        // w + W, ..., several loads in flight; the own cell (j = 0) is also kept as
         // staged.  Warp 0 stores the first 32 attempts' draws; padding records
         // follow the K atoms ----
         if (lane < ns) {
             const int off = G.coff[lane], cnt = G.coff[lane + 1] - off;
             const int4 *src = d.rec[buf] + G.cstart[lane];
-            for (int k0 = wig; k0 < cnt; k0 += SU * W) {
-                int4 v[SU];
+            constexpr int su = W == 2 ? 4 : SU;   // a cell's records in one round trip
+            for (int k0 = wig; k0 < cnt; k0 += su * W) {
+                int4 v[su];
 #pragma unroll
-                for (int u = 0; u < SU; ++u)
+                for (int u = 0; u < su; ++u)
                     if (k0 + u * W < cnt) v[u] = __ldcg(src + k0 + u * W);
 #pragma unroll
-                for (int u = 0; u < SU; ++u) {
+                for (int u = 0; u < su; ++u) {
                     const int k = k0 + u * W;
                     if (k < cnt) {
                         G.rec[off + k] = v[u];
@@ -1429,11 +1430,9 @@ __device__ void run_cell(const DevState &d, int buf, int colour, const LogArgs &
     c.T32 = dy.T32;
     c.gap = md.recheck_gap_f;
     c.err = d.err;
-    float rc2max = 0.f;
-    for (int kk = 0; kk < 9; ++kk) rc2max = fmaxf(rc2max, md.rc2f[kk]);
-    c.pre_r2 = rc2max * 1.01f;
-    c.r2q = c.pre_r2 / c.h2f;
-    const float rconf = rc2max * 1.0201f / c.h2f;   // (1.01 rc)^2, fixed-point units
+    c.pre_r2 = ri.pre_r2;
+    c.r2q = ri.r2q;
+    const float rconf = ri.rconf;   // (1.01 rc)^2, fixed-point units
     c.rv.smem = G.rec;
 
     Tally t{};
