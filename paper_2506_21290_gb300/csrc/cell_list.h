@@ -27,7 +27,7 @@ void launch_phases(const DevState &d, int buf, int warps_per_block, const LogArg
 // the same two stages, separately (for per-stage timing)
 void launch_colour_phases(const DevState &d, int buf, int warps_per_block, const LogArgs &lg, cudaStream_t st);
 void launch_finalize(const DevState &d, cudaStream_t st);
-size_t phase_smem_bytes(int stencil_cap, int rec_cap, int warps_per_cell);
+size_t phase_smem_bytes(int stencil_cap, int warps_per_cell);
 int phase_set_smem_limit(int bytes_needed);
 
 // Persistent sweeps: co-resident blocks for one cooperative launch (0 when the

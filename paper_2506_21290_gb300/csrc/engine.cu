@@ -75,7 +75,6 @@ struct mc_handle {
     int n_cells = 0;
     int n_act = 0;
     int stencil_cap = 0;
-    int own_cap = 0;
     size_t smem_bytes = 0;
     int pgrid = 0;                       // blocks of the persistent sweep (0: CUDA graphs instead)
     unsigned int *d_bar = nullptr;       // grid barrier words
@@ -452,7 +451,7 @@ int create_impl(mc_handle **out, int n_rep, const double *L, const int32_t *n_mo
 
     // layout
     long long sites = 0, cells = 0, act = 0;
-    double max_stencil = 0.0, max_own = 0.0;
+    double max_stencil = 0.0;
     std::vector<int> act_off(n_rep + 1, 0), rep_of_site, rep_of_act;
     for (int r = 0; r < n_rep; ++r) {
         if (n_mol[r] < 1 || n_mol[r] > kMaxMolecules) {
@@ -501,14 +500,12 @@ int create_impl(mc_handle **out, int n_rep, const double *L, const int32_t *n_mo
         act += (long long)(nc / 2) * (nc / 2) * (nc / 2);
         act_off[r + 1] = (int)act;
         rep_of_act.resize(act, r);
-        // neighbourhood and own-cell sizes: mean plus six standard deviations
+        // neighbourhood size: mean plus six standard deviations
         // (counts are at most Poisson-distributed in a liquid) and a margin
         const double per_cell = (double)ri.n_sites / ((double)nc * nc * nc);
         const double mean_nb = 27.0 * per_cell;
         const double st = (nc == 2) ? (double)ri.n_sites : mean_nb + 6.0 * std::sqrt(mean_nb) + 32.0;
         max_stencil = std::max(max_stencil, std::min(st, (double)ri.n_sites));
-        const double own = (nc == 2) ? (double)ri.n_sites : per_cell + 6.0 * std::sqrt(per_cell) + 16.0;
-        max_own = std::max(max_own, std::min(own, (double)ri.n_sites));
         if (sites > (1LL << 30)) {
             delete h;
             return fail(MC_ERR_INVALID_ARG, "too many sites");
@@ -529,8 +526,7 @@ int create_impl(mc_handle **out, int n_rep, const double *L, const int32_t *n_mo
     }
     if (o.warps_per_cell > 0) h->wpb = o.warps_per_cell;
     else h->wpb = h->n_act >= 152 * 12 ? 1 : (h->n_act >= 152 * 3 ? 2 : 4);
-    h->own_cap = std::min(cap, std::max(32, ((int)std::ceil(max_own) + 15) / 16 * 16));
-    h->smem_bytes = phase_smem_bytes(cap, h->own_cap, h->wpb);
+    h->smem_bytes = phase_smem_bytes(cap, h->wpb);
     if (h->smem_bytes > 220u * 1024u) {
         delete h;
         return fail(MC_ERR_INVALID_ARG, "stencil capacity too large for shared memory");
@@ -553,7 +549,6 @@ int create_impl(mc_handle **out, int n_rep, const double *L, const int32_t *n_mo
     d.n_cells = h->n_cells;
     d.n_act = h->n_act;
     d.stencil_cap = cap;
-    d.own_cap = h->own_cap;
     d.precision = h->precision;
     d.wait_limit = o.wait_limit_log2 > 0 ? (1u << o.wait_limit_log2) : 0u;
     const int M_tot = h->n_sites / 3;
@@ -818,7 +813,7 @@ int mc_sweep_timed(mc_handle *h, int n_sweeps, const double *T, const mc_move_mi
 // Switch the cell schedule: warps per cell W and the launch form.
 static int set_schedule(mc_handle *h, int W, bool persistent)
 {
-    const size_t sm = phase_smem_bytes(h->stencil_cap, h->own_cap, W);
+    const size_t sm = phase_smem_bytes(h->stencil_cap, W);
     if (sm > 220u * 1024u) return MC_ERR_INVALID_ARG;
     if (phase_set_smem_limit((int)sm) != 0) return MC_ERR_CUDA;
     if (W != h->wpb)

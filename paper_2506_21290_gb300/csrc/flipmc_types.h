@@ -92,7 +92,6 @@ struct DevState {
     int n_cells;         // total over replicas
     int n_act;           // active cells per colour, total over replicas
     int stencil_cap;     // atoms staged per neighbourhood (plus kPadSlots padding candidates)
-    int own_cap;         // atoms of the own cell a neighbourhood may hold
     int precision;
     unsigned wait_limit; // polls after which a wait between blocks gives up (0: the defaults)
     const RepInfo *rep;

@@ -210,19 +210,28 @@ struct Near {
     float px[6], py[6], pz[6];  // the move's atoms (old and new) relative to the cell centre, fixed-point units
 };
 
-// attempt counts of one warp over one cell
+// Attempt counts of one warp over one cell, one counter per lane: lane l
+// counts stats slot l (l < TALLY_N: attempts and acceptances per move type,
+// geometric and bond rejections, pair evaluations, rechecks).  Every lane
+// holds the outcome of the attempt, so each adds to its own counter and a
+// commit touches no memory for its counts.  Pair evaluations are counted per
+// candidate (2 or 6) and scaled by the neighbourhood size K at the end.
+constexpr int TALLY_N = 12;
+static_assert(STAT_ATT == 0 && STAT_ACC == 4 && STAT_REJ_GEOM == 8 && STAT_REJ_BOND == 9 && STAT_PAIRS == 10 &&
+                  STAT_RECHECK == 11,
+              "lane l of a tally counts stats slot l");
+
+// a warp's counts as the group combines them (W > 1)
 struct Tally {
-    unsigned att[4], acc[4], rej_geom, rej_bond, rechecks;
+    unsigned cnt[TALLY_N];
+    unsigned inter;             // pair-potential evaluations inside their range (summed over the warp's lanes)
     float dEf;                  // FP32 mode: accepted Delta E, in commit order
-    unsigned long long pairs;
-    unsigned long long inter;   // pair-potential evaluations inside their range (summed over the warp's lanes)
     double dE;                  // FP64 mode: accepted Delta E, in commit order
 };
 
 struct Group {
     int4 *rec;                  // [cap] raw records {qx, qy, qz, w} of the neighbourhood, own cell first,
                                 //       then kPadSlots padding records
-    int4 *orig;                 // [own_cap] the own cell as staged (periodic images at write-back)
     uint64_t *mbar;             // completion barrier of the bulk copies that stage rec (W = 1)
     uint32_t *rnd;              // [32 * 8] random words of a chunk of attempts
     double *thr64;              // [32]
@@ -231,7 +240,7 @@ struct Group {
     int *coff;                  // [32]
     int *misc;                  // [32]
     Near *near;                 // [W]
-    Tally *tally;               // [W]
+    Tally *tally;               // [W] each warp's counts over the cell, combined at its end (W > 1)
     unsigned char *warp_base;   // W per-warp scratch blocks
 };
 
@@ -239,22 +248,29 @@ enum { MS_K = 0, MS_N = 1, MS_START = 2, MS_PHASE = 3, MS_CLASH = 4 /* [W <= 8] 
 
 __host__ __device__ constexpr size_t al16(size_t x) { return (x + 15) & ~size_t(15); }
 
-__host__ __device__ inline size_t warp_scr_bytes()
+__host__ __device__ constexpr size_t warp_scr_bytes()
 {
-    const size_t q = al16(sizeof(int) * (QW + 1));
-    const size_t k = al16(sizeof(unsigned long long) * TERM_CAP);
-    return (q > k ? q : k) + al16(sizeof(double) * TERM_CAP) + al16(sizeof(int) * 4);
+    return (al16(sizeof(int) * (QW + 1)) > al16(sizeof(unsigned long long) * TERM_CAP)
+                ? al16(sizeof(int) * (QW + 1))
+                : al16(sizeof(unsigned long long) * TERM_CAP)) +
+           al16(sizeof(double) * TERM_CAP) + al16(sizeof(int) * 4);
 }
 
-__host__ __device__ inline size_t group_bytes(int cap, int own_cap, int W)
+// Layout of a group's shared memory: the fixed-size parts first (at offsets
+// known at compile time for each W), the neighbourhood records last.
+__host__ __device__ constexpr size_t group_fixed_bytes(int W)
 {
-    return al16(sizeof(int4) * cap) + al16(sizeof(int4) * own_cap) + 16 +
-           al16(sizeof(uint32_t) * 256) +
-           al16(sizeof(double) * 32) + al16(sizeof(float) * 32) + 3 * al16(sizeof(int) * 32) +
-           al16(sizeof(Near) * W) + al16(sizeof(Tally) * W) + (size_t)W * warp_scr_bytes();
+    return 16 + al16(sizeof(uint32_t) * 256) + al16(sizeof(double) * 32) + al16(sizeof(float) * 32) +
+           3 * al16(sizeof(int) * 32) + al16(sizeof(Near) * W) + al16(sizeof(Tally) * W) +
+           (size_t)W * warp_scr_bytes();
 }
 
-__device__ inline Group carve(unsigned char *base, int cap, int own_cap, int W)
+__host__ __device__ inline size_t group_bytes(int cap, int W)
+{
+    return group_fixed_bytes(W) + al16(sizeof(int4) * cap);
+}
+
+__device__ inline Group carve(unsigned char *base, int W)
 {
     Group s;
     size_t o = 0;
@@ -263,8 +279,6 @@ __device__ inline Group carve(unsigned char *base, int cap, int own_cap, int W)
         o += al16(bytes);
         return p;
     };
-    s.rec = (int4 *)take(sizeof(int4) * cap);
-    s.orig = (int4 *)take(sizeof(int4) * own_cap);
     s.mbar = (uint64_t *)take(16);
     s.rnd = (uint32_t *)take(sizeof(uint32_t) * 256);
     s.thr64 = (double *)take(sizeof(double) * 32);
@@ -274,7 +288,8 @@ __device__ inline Group carve(unsigned char *base, int cap, int own_cap, int W)
     s.misc = (int *)take(sizeof(int) * 32);
     s.near = (Near *)take(sizeof(Near) * W);
     s.tally = (Tally *)take(sizeof(Tally) * W);
-    s.warp_base = base + o;
+    s.warp_base = take((size_t)W * warp_scr_bytes());
+    s.rec = (int4 *)(base + o);
     return s;
 }
 
@@ -1113,28 +1128,31 @@ __device__ __forceinline__ bool clashes(const Near *near, int wb, float rconf, i
     return __any_sync(FULL, hit);
 }
 
-// Apply attempt R (number `at` in the cell) to the staged state, count it, log
-// it.  One thread (lane 0 of the warp that evaluated it).
-template <int PREC>
-__device__ __forceinline__ void commit(const Group &G, const Res &R, int at, int K, Tally &t, const LogArgs &lg,
-                                       const RepInfo &ri, uint64_t sweep, int own_start)
+// This lane's count of attempt R (see Tally).
+__device__ __forceinline__ unsigned tally_inc(const Res &R, int lane)
 {
-#pragma unroll
-    for (int m = 0; m < 4; ++m) {   // static indices keep the counts in registers
-        t.att[m] += R.mvt == m;
-        t.acc[m] += (R.mvt == m) & (R.accept != 0);
-    }
-    if (R.status == MC_ST_LEFT_CELL || R.status == MC_ST_NOT_IN_CELL) t.rej_geom += 1;
-    if (R.status == MC_ST_BOND_BREAK) t.rej_bond += 1;
-    if (R.status == MC_ST_EVALUATED || R.status == MC_ST_BOND_BREAK)
-        t.pairs += (unsigned long long)R.pairs * (unsigned long long)K;
-    t.rechecks += R.flags;
+    const bool evaluated = R.status == MC_ST_EVALUATED || R.status == MC_ST_BOND_BREAK;
+    const bool geom = R.status == MC_ST_LEFT_CELL || R.status == MC_ST_NOT_IN_CELL;
+    unsigned inc = lane == STAT_ATT + R.mvt;
+    inc += (lane == STAT_ACC + R.mvt) & (R.accept != 0);
+    inc += (lane == STAT_REJ_GEOM) & geom;
+    inc += (lane == STAT_REJ_BOND) & (R.status == MC_ST_BOND_BREAK);
+    inc += (lane == STAT_PAIRS) & evaluated ? (unsigned)R.pairs : 0u;
+    inc += (lane == STAT_RECHECK) ? (unsigned)R.flags : 0u;
+    return inc;
+}
+
+// Apply attempt R (number `at` in the cell) to the staged state and log it.
+// One thread (lane 0 of the warp that evaluated it).  A moved atom whose
+// fixed-point coordinate wraps around the box counts the periodic image it
+// enters (img, per global site): only the cell that owns the atom moves it,
+// so the counts need no atomics, and the per-commit wraps add up to those of
+// the cell's net displacement.
+template <int PREC>
+__device__ __forceinline__ void commit(const Group &G, const Res &R, int at, const LogArgs &lg, const RepInfo &ri,
+                                       uint64_t sweep, int own_start, int *img)
+{
     if (R.accept) {
-        // the running energy: FP64 sums in FP64 mode; in FP32 mode the few
-        // accepted Delta E of a cell are summed in FP32 (they carry FP32
-        // errors already) and the cell total joins the FP64 sum
-        if (PREC == MC_PREC_FP64) t.dE = __dadd_rn(t.dE, R.dE64);
-        else t.dEf += R.flags ? (float)R.dE64 : R.dE32;
         if (R.mvt == MC_MOVE_FLIP) {
 #pragma unroll
             for (int s = 0; s < 2; ++s) {
@@ -1148,6 +1166,14 @@ __device__ __forceinline__ void commit(const Group &G, const Res &R, int at, int
                 if (s < R.nmv) {
                     const int ks = R.ks[s];
                     int4 rs = G.rec[ks];
+                    const uint32_t o3[3] = {(uint32_t)rs.x, (uint32_t)rs.y, (uint32_t)rs.z};
+                    int *im = img + 3 * (size_t)(ri.site_off + rec_site(rs.w));
+#pragma unroll
+                    for (int ax = 0; ax < 3; ++ax) {
+                        const long long moved = (long long)o3[ax] + (long long)(int)(R.qn[s][ax] - o3[ax]);
+                        if (moved < 0) im[ax] -= 1;
+                        else if (moved >= 4294967296ll) im[ax] += 1;
+                    }
                     rs.x = (int)R.qn[s][0];
                     rs.y = (int)R.qn[s][1];
                     rs.z = (int)R.qn[s][2];
@@ -1188,7 +1214,7 @@ __device__ __forceinline__ void load_tables(const DevState &d, ModelDev &md, Mix
 __device__ __forceinline__ void init_group(unsigned char *gsmem, const DevState &d, int W)
 {
     if (threadIdx.x % (32 * W) == 0) {
-        const Group G = carve(gsmem, d.stencil_cap, d.own_cap, W);
+        const Group G = carve(gsmem, W);
         mbar_init(G.mbar);
         G.misc[MS_PHASE] = 0;
     }
@@ -1236,8 +1262,7 @@ __device__ void run_cell(const DevState &d, int buf, int colour, const LogArgs &
     const int lane = threadIdx.x & 31;
     const int wig = gt >> 5;
     const int cap = d.stencil_cap;
-    const int own_cap = d.own_cap;
-    const Group G = carve(gsmem, cap, own_cap, W);
+    const Group G = carve(gsmem, W);
     const WarpScr S = warp_scr(G, wig);
 
     // ---- which cell ----
@@ -1311,8 +1336,8 @@ __device__ void run_cell(const DevState &d, int buf, int colour, const LogArgs &
         if constexpr (W == 1) {
             // one-warp groups stage by bulk copies, one per cell, all
             // completing on the group's barrier (only when they fit)
-            const int Kw = __shfl_sync(FULL, incl, 31), nw0 = __shfl_sync(FULL, cnt, 0);
-            if (Kw + PADS <= cap && nw0 <= own_cap) {
+            const int Kw = __shfl_sync(FULL, incl, 31);
+            if (Kw + PADS <= cap) {
                 if (lane == 0) mbar_arrive_expect(G.mbar, 16u * (unsigned)Kw);
                 __syncwarp();
                 if (lane < ns && cnt > 0)
@@ -1324,7 +1349,7 @@ __device__ void run_cell(const DevState &d, int buf, int colour, const LogArgs &
     const int K = G.misc[MS_K];
     const int n = G.misc[MS_N];
     const int own_start = G.misc[MS_START];
-    if (K + PADS > cap || n > own_cap) {   // the neighbourhood does not fit: nothing is staged
+    if (K + PADS > cap) {   // the neighbourhood does not fit: nothing is staged
         if (gt == 0) {
             atomicOr(d.err, ERR_STENCIL);
             d.cell_dE[cellG] = 0.0;
@@ -1334,8 +1359,8 @@ __device__ void run_cell(const DevState &d, int buf, int colour, const LogArgs &
     }
 
     if constexpr (W == 1) {
-        // ---- stage (one warp): wait for the bulk copies (bounded), keep a copy
-        // of the own cell, store the first 32 attempts' draws; padding records
+        // ---- stage (one warp): wait for the bulk copies (bounded), store the
+        // first 32 attempts' draws; padding records
         // follow the K atoms (no molecule, never within reach: the screens and
         // the interaction passes read them instead of branching) ----
         const unsigned parity = (unsigned)G.misc[MS_PHASE];
@@ -1348,7 +1373,6 @@ __device__ void run_cell(const DevState &d, int buf, int colour, const LogArgs &
             }
         }
         if (!ok) G.misc[MS_FAIL] = 1;
-        for (int idx = lane; ok && idx < n; idx += 32) G.orig[idx] = G.rec[idx];   // the own cell as staged
         if (lane < n) {
             uint4 *wv = (uint4 *)(G.rnd + 8 * lane);
             wv[0] = rb0;
@@ -1373,8 +1397,8 @@ __device__ void run_cell(const DevState &d, int buf, int colour, const LogArgs &
         // loaded straight from L2 (the waits above acquired the neighbours'
         // writes; .cg loads bypass L1, which may hold lines of an earlier
         // phase).  Lane j of every warp takes cell j, warp w its records w,
-        // w + W, ..., several loads in flight; the own cell (j = 0) is also kept as
-        // staged.  Warp 0 stores the first 32 attempts' draws; padding records
+        // w + W, ..., several loads in flight.  Warp 0 stores the first 32
+        // attempts' draws; padding records
         // follow the K atoms ----
         if (lane < ns) {
             const int off = G.coff[lane], cnt = G.coff[lane + 1] - off;
@@ -1388,10 +1412,7 @@ __device__ void run_cell(const DevState &d, int buf, int colour, const LogArgs &
 #pragma unroll
                 for (int u = 0; u < su; ++u) {
                     const int k = k0 + u * W;
-                    if (k < cnt) {
-                        G.rec[off + k] = v[u];
-                        if (lane == 0) G.orig[k] = v[u];
-                    }
+                    if (k < cnt) G.rec[off + k] = v[u];
                 }
             }
         }
@@ -1418,7 +1439,7 @@ __device__ void run_cell(const DevState &d, int buf, int colour, const LogArgs &
     c.shift[2] = ct.shift[2];
     // origin of the conflict test's frame: any point near the cell will do (the
     // test compares differences with a 1% margin); own atom 0 as staged
-    const int4 p0 = n > 0 ? G.orig[0] : make_int4(0, 0, 0, 0);
+    const int4 p0 = n > 0 ? G.rec[0] : make_int4(0, 0, 0, 0);
     c.P[0] = (uint32_t)p0.x;
     c.P[1] = (uint32_t)p0.y;
     c.P[2] = (uint32_t)p0.z;
@@ -1435,8 +1456,13 @@ __device__ void run_cell(const DevState &d, int buf, int colour, const LogArgs &
     const float rconf = ri.rconf;   // (1.01 rc)^2, fixed-point units
     c.rv.smem = G.rec;
 
-    Tally t{};
+    unsigned cnt = 0;                  // this lane's counter of the warp's tally
     unsigned inter_lane = 0;           // this lane's share of the committed attempts' in-range evaluations
+    // the running energy: FP64 sums in FP64 mode; in FP32 mode the few
+    // accepted Delta E of a cell are summed in FP32 (they carry FP32 errors
+    // already) and the cell total joins the FP64 sum (every lane the same)
+    float dEf = 0.f;
+    double dE = 0.0;
     for (int a0 = 0; a0 < n; a0 += 32) {
         if (a0 > 0) {
             // random words and thresholds of the next chunk (cells with more than 32 atoms)
@@ -1486,71 +1512,57 @@ __device__ void run_cell(const DevState &d, int buf, int colour, const LogArgs &
                 __syncwarp();
             }
             // committed attempts touch different molecules: each warp applies its own
-            if (wig < adv && lane == 0) commit<PREC>(G, R, a + wig, K, t, lg, ri, ct.sweep, own_start);
-            if (wig < adv) inter_lane += (unsigned)R.inter;
+            if (wig < adv) {
+                if (lane == 0) commit<PREC>(G, R, a + wig, lg, ri, ct.sweep, own_start, d.img);
+                cnt += tally_inc(R, lane);
+                inter_lane += (unsigned)R.inter;
+                if (R.accept) {
+                    if (PREC == MC_PREC_FP64) dE = __dadd_rn(dE, R.dE64);
+                    else dEf += R.flags ? (float)R.dE64 : R.dE32;
+                }
+            }
             if constexpr (W > 1) gsync<W>(gid);
             else __syncwarp();
             a += adv;
         }
     }
 
-    // ---- write back the cell; count periodic images crossed ----
+    // ---- write back the cell ----
     int4 *dst = d.rec[buf] + own_start;
-    for (int kk = gt; kk < n; kk += T) {
-        const int4 nw = G.rec[kk];
-        const int4 od = G.orig[kk];
-        const int site = ri.site_off + rec_site(nw.w);
-        const uint32_t o3[3] = {(uint32_t)od.x, (uint32_t)od.y, (uint32_t)od.z};
-        const uint32_t n3[3] = {(uint32_t)nw.x, (uint32_t)nw.y, (uint32_t)nw.z};
-#pragma unroll
-        for (int ax = 0; ax < 3; ++ax) {
-            const long long moved = (long long)o3[ax] + (long long)(int)(n3[ax] - o3[ax]);
-            if (moved < 0) d.img[3 * site + ax] -= 1;
-            else if (moved >= 4294967296ll) d.img[3 * site + ax] += 1;
-        }
-        dst[kk] = nw;
-    }
+    for (int kk = gt; kk < n; kk += T) dst[kk] = G.rec[kk];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) inter_lane += __shfl_xor_sync(FULL, inter_lane, o);
-    t.inter = inter_lane;
+    if constexpr (W > 1) {
+        Tally &u = G.tally[wig];
+        if (lane < TALLY_N) u.cnt[lane] = cnt;
+        if (lane == 0) {
+            u.inter = inter_lane;
+            u.dEf = dEf;
+            u.dE = dE;
+        }
+    }
     // ---- publish the cell to the neighbours waiting for it (before the
     // counts, which nobody waits for); then the warps' tallies in warp order ----
-    if constexpr (W > 1) {
-        if (lane == 0) G.tally[wig] = t;
-        gsync<W>(gid);   // every write-back and tally is done
-    } else {
-        __syncwarp();
-    }
+    gsync<W>(gid);   // every write-back and tally is done
     if (gt == 0 && dep != 0) signal_done(d.cell_done + cellG);
-    if constexpr (W > 1) {
-        if (gt == 0)
+    if (wig == 0) {
+        if constexpr (W > 1) {
             for (int j = 1; j < W; ++j) {
                 const Tally &u = G.tally[j];
-                for (int m = 0; m < 4; ++m) {
-                    t.att[m] += u.att[m];
-                    t.acc[m] += u.acc[m];
-                }
-                t.rej_geom += u.rej_geom;
-                t.rej_bond += u.rej_bond;
-                t.rechecks += u.rechecks;
-                t.pairs += u.pairs;
-                t.inter += u.inter;
-                if (PREC == MC_PREC_FP64) t.dE = __dadd_rn(t.dE, u.dE);
-                else t.dEf += u.dEf;
+                if (lane < TALLY_N) cnt += u.cnt[lane];
+                inter_lane += u.inter;
+                if (PREC == MC_PREC_FP64) dE = __dadd_rn(dE, u.dE);
+                else dEf += u.dEf;
             }
-    }
-    if (gt == 0) {
-        d.cell_dE[cellG] = PREC == MC_PREC_FP64 ? t.dE : (double)t.dEf;
-        unsigned long long *st = d.stats + (size_t)r * STAT_N;
-        for (int m = 0; m < 4; ++m) {
-            if (t.att[m]) atomicAdd(st + STAT_ATT + m, (unsigned long long)t.att[m]);
-            if (t.acc[m]) atomicAdd(st + STAT_ACC + m, (unsigned long long)t.acc[m]);
         }
-        if (t.rej_geom) atomicAdd(st + STAT_REJ_GEOM, (unsigned long long)t.rej_geom);
-        if (t.rej_bond) atomicAdd(st + STAT_REJ_BOND, (unsigned long long)t.rej_bond);
-        if (t.pairs) atomicAdd(st + STAT_PAIRS, t.pairs);
-        if (t.inter) atomicAdd(st + STAT_INTER, t.inter);
-        if (t.rechecks) atomicAdd(st + STAT_RECHECK, (unsigned long long)t.rechecks);
+        unsigned long long *st = d.stats + (size_t)r * STAT_N;
+        const unsigned long long v =
+            lane == STAT_PAIRS ? (unsigned long long)cnt * (unsigned long long)K : (unsigned long long)cnt;
+        if (lane < TALLY_N && v != 0) atomicAdd(st + lane, v);
+        if (lane == 0) {
+            if (inter_lane) atomicAdd(st + STAT_INTER, (unsigned long long)inter_lane);
+            d.cell_dE[cellG] = PREC == MC_PREC_FP64 ? dE : (double)dEf;
+        }
     }
 }
 
@@ -1565,7 +1577,7 @@ __global__ void __launch_bounds__(block_threads<W>(), W == 1 ? 3 : 1) phase_kern
     __shared__ ModelDev md;
     __shared__ MixDev mx;
     const int gid = threadIdx.x / (32 * W);
-    unsigned char *gsmem = smem + (size_t)gid * group_bytes(d.stencil_cap, d.own_cap, W);
+    unsigned char *gsmem = smem + (size_t)gid * group_bytes(d.stencil_cap, W);
     init_group(gsmem, d, W);
     load_tables(d, md, mx);
     __syncthreads();
@@ -1693,7 +1705,7 @@ __global__ void __launch_bounds__(block_threads<W>(), W == 1 ? 3 : 1) sweep_pers
     __shared__ double red[BLOCK];
     __shared__ int tmp[NT / 32];
     const int gid = threadIdx.x / T;
-    unsigned char *gsmem = smem + (size_t)gid * group_bytes(d.stencil_cap, d.own_cap, W);
+    unsigned char *gsmem = smem + (size_t)gid * group_bytes(d.stencil_cap, W);
     init_group(gsmem, d, W);
     load_tables(d, md, mx);
     __syncthreads();
@@ -1790,10 +1802,10 @@ int sweep_binary_version()
     return a.binaryVersion;
 }
 
-size_t phase_smem_bytes(int stencil_cap, int own_cap, int warps_per_cell)
+size_t phase_smem_bytes(int stencil_cap, int warps_per_cell)
 {
     const int nt = warps_per_cell > 4 ? 32 * warps_per_cell : BLOCK;
-    return group_bytes(stencil_cap, own_cap, warps_per_cell) * (size_t)(nt / (32 * warps_per_cell));
+    return group_bytes(stencil_cap, warps_per_cell) * (size_t)(nt / (32 * warps_per_cell));
 }
 
 template <class K>
@@ -1843,7 +1855,7 @@ static void launch_prec(const DevState &d, int buf, int W, const LogArgs &lg, cu
     const int nt = W > 4 ? 32 * W : BLOCK;
     const int cpb = nt / (32 * W);
     const int blocks = (d.n_act + cpb - 1) / cpb;
-    const size_t sm = phase_smem_bytes(d.stencil_cap, d.own_cap, W);
+    const size_t sm = phase_smem_bytes(d.stencil_cap, W);
     for (int colour = 0; colour < 8; ++colour) {
         if (W == 8) phase_kernel<PREC, 8><<<blocks, 256, sm, st>>>(d, buf, colour, lg);
         else if (W == 4) phase_kernel<PREC, 4><<<blocks, BLOCK, sm, st>>>(d, buf, colour, lg);
@@ -1895,7 +1907,7 @@ int persistent_grid(const DevState &d, int warps_per_cell, int max_blocks)
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
     if (!coop) return 0;
-    const size_t sm = phase_smem_bytes(d.stencil_cap, d.own_cap, warps_per_cell);
+    const size_t sm = phase_smem_bytes(d.stencil_cap, warps_per_cell);
     const int nt = warps_per_cell > 4 ? 32 * warps_per_cell : BLOCK;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_kernel(d.precision, warps_per_cell), nt, sm) !=
         cudaSuccess)
@@ -1910,7 +1922,7 @@ int persistent_grid(const DevState &d, int warps_per_cell, int max_blocks)
 int launch_persistent(const DevState &d, int buf, int n_sweeps, int warps_per_cell, int grid, unsigned int *bar,
                       int *scan_tot, cudaStream_t st)
 {
-    const size_t sm = phase_smem_bytes(d.stencil_cap, d.own_cap, warps_per_cell);
+    const size_t sm = phase_smem_bytes(d.stencil_cap, warps_per_cell);
     GridBar gb{bar, scan_tot};
     DevState dd = d;
     void *args[] = {(void *)&dd, (void *)&buf, (void *)&n_sweeps, (void *)&gb};
