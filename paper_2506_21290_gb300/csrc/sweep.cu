@@ -1313,7 +1313,9 @@ __device__ void run_cell(const DevState &d, int buf, int colour, const LogArgs &
                 else th32 = d.att_thr32[slot];
             }
         }
-        if (wait_c >= 0) wait_done(d.cell_done + wait_c, dep, d.err, d.wait_limit);
+        // one-warp groups wait before the offsets, multi-warp groups after
+        // (each order measured faster for its schedule)
+        if (W == 1 && wait_c >= 0) wait_done(d.cell_done + wait_c, dep, d.err, d.wait_limit);
         int incl = cnt;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -1333,6 +1335,8 @@ __device__ void run_cell(const DevState &d, int buf, int colour, const LogArgs &
             G.misc[MS_START] = cst;
             G.misc[MS_FAIL] = 0;
         }
+        if (W > 1 && wait_c >= 0) wait_done(d.cell_done + wait_c, dep, d.err, d.wait_limit);
+        __syncwarp();
         if constexpr (W == 1) {
             // one-warp groups stage by bulk copies, one per cell, all
             // completing on the group's barrier (only when they fit)
@@ -1403,7 +1407,7 @@ __device__ void run_cell(const DevState &d, int buf, int colour, const LogArgs &
         if (lane < ns) {
             const int off = G.coff[lane], cnt = G.coff[lane + 1] - off;
             const int4 *src = d.rec[buf] + G.cstart[lane];
-            constexpr int su = W == 2 ? 4 : SU;   // a cell's records in one round trip
+            constexpr int su = W == 2 ? 8 : (W == 4 ? 4 : SU);   // a cell's records in one round trip
             for (int k0 = wig; k0 < cnt; k0 += su * W) {
                 int4 v[su];
 #pragma unroll
@@ -1527,12 +1531,21 @@ __device__ void run_cell(const DevState &d, int buf, int colour, const LogArgs &
         }
     }
 
-    // ---- write back the cell ----
+    // ---- write back the cell and publish it to the neighbours waiting for
+    // it; then the counts, which nobody waits for: the warps' tallies in warp
+    // order (one-warp groups reduce their lanes' counts before publishing,
+    // multi-warp groups after: each order measured faster for its schedule) ----
     int4 *dst = d.rec[buf] + own_start;
     for (int kk = gt; kk < n; kk += T) dst[kk] = G.rec[kk];
+    if constexpr (W == 1) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) inter_lane += __shfl_xor_sync(FULL, inter_lane, o);
+        for (int o = 16; o > 0; o >>= 1) inter_lane += __shfl_xor_sync(FULL, inter_lane, o);
+    }
+    gsync<W>(gid);   // every write-back is done
+    if (gt == 0 && dep != 0) signal_done(d.cell_done + cellG);
     if constexpr (W > 1) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) inter_lane += __shfl_xor_sync(FULL, inter_lane, o);
         Tally &u = G.tally[wig];
         if (lane < TALLY_N) u.cnt[lane] = cnt;
         if (lane == 0) {
@@ -1540,11 +1553,8 @@ __device__ void run_cell(const DevState &d, int buf, int colour, const LogArgs &
             u.dEf = dEf;
             u.dE = dE;
         }
+        gsync<W>(gid);   // every tally is written
     }
-    // ---- publish the cell to the neighbours waiting for it (before the
-    // counts, which nobody waits for); then the warps' tallies in warp order ----
-    gsync<W>(gid);   // every write-back and tally is done
-    if (gt == 0 && dep != 0) signal_done(d.cell_done + cellG);
     if (wig == 0) {
         if constexpr (W > 1) {
             for (int j = 1; j < W; ++j) {
