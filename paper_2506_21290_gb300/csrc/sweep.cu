@@ -553,27 +553,34 @@ __device__ __forceinline__ void queue_step(const WarpScr &S, int lane, int &qlen
     qlen += __popc(b);
 }
 
-// The K candidates in screening blocks: 4 steps while more than 192 remain
-// (only the last step can reach past K), then one block of the 1 to 3 steps
-// that cover the rest.
-template <class Steps>
+// The K candidates in screening blocks.  WHOLE (one-warp groups, where the
+// smaller code measured faster): 4-step blocks only, every step clamped to
+// K.  Otherwise 4 steps while more than 192 candidates remain (only the last
+// step can reach past K), then one block of the 1 to 3 steps that cover the
+// rest.
+template <bool WHOLE, class Steps>
 __device__ __forceinline__ int screen_blocks(int K, const Steps &st)
 {
     int qlen = 0, base = 0;
-    for (; K - base > 64 * (SCREEN_U - 1); base += 64 * SCREEN_U) st.template run<SCREEN_U>(base, qlen);
-    const int rem = (K - base + 63) >> 6;   // 0 to 3
-    if (rem == 3) st.template run<3>(base, qlen);
-    else if (rem == 2) st.template run<2>(base, qlen);
-    else if (rem == 1) st.template run<1>(base, qlen);
+    if constexpr (WHOLE) {
+        for (; base < K; base += 64 * SCREEN_U) st.template run<SCREEN_U, true>(base, qlen);
+    } else {
+        for (; K - base > 64 * (SCREEN_U - 1); base += 64 * SCREEN_U) st.template run<SCREEN_U, false>(base, qlen);
+        const int rem = (K - base + 63) >> 6;   // 0 to 3
+        if (rem == 3) st.template run<3, false>(base, qlen);
+        else if (rem == 2) st.template run<2, false>(base, qlen);
+        else if (rem == 1) st.template run<1, false>(base, qlen);
+    }
     return qlen;
 }
 
 // candidate pair of step u of a block: below K except in the block's last step
-template <int U>
+// (or in any step, CLAMP)
+template <int U, bool CLAMP>
 __device__ __forceinline__ void step_pair(const Group &G, int K, int base, int u, int lane, int4 &r0, int4 &r1)
 {
     int c0 = base + 64 * u + lane, c1 = c0 + 32;
-    if (u == U - 1) {
+    if (CLAMP || u == U - 1) {
         c0 = min(c0, K);
         c1 = min(c1, K);
     }
@@ -591,14 +598,14 @@ struct AtomSteps {
     Q3 qo;
     f2_t mx, my, mz, e2;
     float r2q;
-    template <int U>
+    template <int U, bool CLAMP>
     __device__ __forceinline__ void run(int base, int &qlen) const
     {
         unsigned b0[U], b1[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             int4 r0, r1;
-            step_pair<U>(G, K, base, u, lane, r0, r1);
+            step_pair<U, CLAMP>(G, K, base, u, lane, r0, r1);
             const f2_t X = pk(dq((uint32_t)r0.x, qo.x), dq((uint32_t)r1.x, qo.x));
             const f2_t Y = pk(dq((uint32_t)r0.y, qo.y), dq((uint32_t)r1.y, qo.y));
             const f2_t Z = pk(dq((uint32_t)r0.z, qo.z), dq((uint32_t)r1.z, qo.z));
@@ -617,6 +624,7 @@ struct AtomSteps {
     }
 };
 
+template <bool WHOLE>
 __device__ __forceinline__ int screen_atom(const Group &G, const WarpScr &S, int K, int lane, const Q3 &qo,
                                            const Q3 &qn, int wi, float r2q)
 {
@@ -624,7 +632,7 @@ __device__ __forceinline__ int screen_atom(const Group &G, const WarpScr &S, int
     const float ee = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
     const AtomSteps st{G, S, K, lane, wi, qo, pk(-2.f * ex, -2.f * ex), pk(-2.f * ey, -2.f * ey),
                        pk(-2.f * ez, -2.f * ez), pk(ee, ee), r2q};
-    return screen_blocks(K, st);
+    return screen_blocks<WHOLE>(K, st);
 }
 
 // Flip: distance of every candidate to the two atoms whose types swap.
@@ -634,14 +642,14 @@ struct FlipSteps {
     int K, lane, wi;
     Q3 qp, qq;
     float r2q;
-    template <int U>
+    template <int U, bool CLAMP>
     __device__ __forceinline__ void run(int base, int &qlen) const
     {
         unsigned b0[U], b1[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             int4 r0, r1;
-            step_pair<U>(G, K, base, u, lane, r0, r1);
+            step_pair<U, CLAMP>(G, K, base, u, lane, r0, r1);
             f2_t X = pk(dq((uint32_t)r0.x, qp.x), dq((uint32_t)r1.x, qp.x));
             f2_t Y = pk(dq((uint32_t)r0.y, qp.y), dq((uint32_t)r1.y, qp.y));
             f2_t Z = pk(dq((uint32_t)r0.z, qp.z), dq((uint32_t)r1.z, qp.z));
@@ -663,11 +671,12 @@ struct FlipSteps {
     }
 };
 
+template <bool WHOLE>
 __device__ __forceinline__ int screen_flip(const Group &G, const WarpScr &S, int K, int lane, const Q3 &qp,
                                            const Q3 &qq, int wi, float r2q)
 {
     const FlipSteps st{G, S, K, lane, wi, qp, qq, r2q};
-    return screen_blocks(K, st);
+    return screen_blocks<WHOLE>(K, st);
 }
 
 // Rigid molecule move: the three atoms, old and new (molecule partners are
@@ -1007,9 +1016,9 @@ __device__ Res evaluate(const CellCtx &cx, const Group &G, const WarpScr &S, Nea
     if (status == MC_ST_EVALUATED) {
         int qlen;
         if (mvt == MC_MOVE_ATOM) {
-            qlen = screen_atom(G, S, K, lane, qo[0], qn[0], wi, cx.r2q);
+            qlen = screen_atom<W == 1>(G, S, K, lane, qo[0], qn[0], wi, cx.r2q);
         } else if (mvt == MC_MOVE_FLIP) {
-            qlen = screen_flip(G, S, K, lane, qo[0], qo[1], wi, cx.r2q);
+            qlen = screen_flip<W == 1>(G, S, K, lane, qo[0], qo[1], wi, cx.r2q);
         } else {
             const Q3 a[3] = {qo[0], qo[1], qo[2]}, b[3] = {qn[0], qn[1], qn[2]};
             qlen = screen_mol(G, S, K, lane, a, b, wi, cx.r2q);
