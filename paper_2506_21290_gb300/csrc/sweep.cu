@@ -1229,12 +1229,18 @@ __device__ __forceinline__ void init_group(unsigned char *gsmem, const DevState 
     }
 }
 
-// Ordering of the colour phases inside one persistent launch, cell by cell:
-// a cell may start its phase of sweep s once every neighbour cell of a smaller
-// colour has finished its phase of sweep s (the neighbours' writes are then
-// visible, and none of them still reads this cell's atoms; neighbours of a
-// larger colour wait for this cell in turn).  done[c] counts the phases cell c
-// completed in the launch; dep = s + 1 (0: ordered by kernel boundaries).
+// Ordering inside one persistent launch, cell by cell: a cell may start its
+// phase of sweep s once every neighbour of a smaller colour has finished its
+// phase (the neighbours' writes are then visible, and none of them still reads
+// this cell's atoms; neighbours of a larger colour wait for this cell in turn).
+// done[c] counts what cell c completed in the launch.  One-warp groups: its
+// colour phases (s + 1 after sweep s), the cell list being complete at a grid
+// barrier.  Multi-warp groups: its order passes too, two per sweep (2s + 1 once
+// it is ordered in sweep s, 2s + 2 after its phase), and a phase also waits
+// for every cell of its neighbourhood, itself included, to be ordered (no grid
+// barrier between the order pass and the colours; measured faster for these
+// schedules and slower for one-warp groups).  In run_cell, dep = s + 1 (0:
+// ordered by kernel boundaries); wait_done waits for done[c] >= a count.
 __device__ __forceinline__ void wait_done(const unsigned int *done, unsigned dep, int *err, unsigned limit)
 {
     const unsigned lim = limit ? limit : (1u << 21);
@@ -1297,6 +1303,7 @@ __device__ void run_cell(const DevState &d, int buf, int colour, const LogArgs &
     float th32 = 0.f;
     if (wig == 0) {
         int cnt = 0, cst = 0, wait_c = -1;
+        unsigned wait_n = 0;
         if (lane < ns) {
             int ox, oy, oz;
             if (raw) {
@@ -1308,7 +1315,13 @@ __device__ void run_cell(const DevState &d, int buf, int colour, const LogArgs &
             const int nx = (cx + ox + nc) % nc, ny = (cy + oy + nc) % nc, nz = (cz + oz + nc) % nc;
             const int c = ri.cell_off + (nz * nc + ny) * nc + nx;
             const int ncol = (nx & 1) | ((ny & 1) << 1) | ((nz & 1) << 2);
-            if (dep != 0 && ncol < colour) wait_c = c;
+            if (W == 1) {
+                if (dep != 0 && ncol < colour) wait_c = c;
+                wait_n = dep;
+            } else {
+                if (dep != 0) wait_c = c;
+                wait_n = ncol < colour ? 2u * dep : 2u * dep - 1u;
+            }
             cst = d.cell_start[c];
             cnt = d.cell_start[c + 1] - cst;
         }
@@ -1324,7 +1337,7 @@ __device__ void run_cell(const DevState &d, int buf, int colour, const LogArgs &
         }
         // one-warp groups wait before the offsets, multi-warp groups after
         // (each order measured faster for its schedule)
-        if (W == 1 && wait_c >= 0) wait_done(d.cell_done + wait_c, dep, d.err, d.wait_limit);
+        if (W == 1 && wait_c >= 0) wait_done(d.cell_done + wait_c, wait_n, d.err, d.wait_limit);
         int incl = cnt;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -1344,7 +1357,7 @@ __device__ void run_cell(const DevState &d, int buf, int colour, const LogArgs &
             G.misc[MS_START] = cst;
             G.misc[MS_FAIL] = 0;
         }
-        if (W > 1 && wait_c >= 0) wait_done(d.cell_done + wait_c, dep, d.err, d.wait_limit);
+        if (W > 1 && wait_c >= 0) wait_done(d.cell_done + wait_c, wait_n, d.err, d.wait_limit);
         __syncwarp();
         if constexpr (W == 1) {
             // one-warp groups stage by bulk copies, one per cell, all
@@ -1749,21 +1762,33 @@ __global__ void __launch_bounds__(block_threads<W>(), W == 1 ? 3 : 1) sweep_pers
     for (int s = 0; s < n_sweeps; ++s) {
         int *const cnt = (s & 1) ? d.cell_count2 : d.cell_count;
         if (!grid_sync(gb, bar_target, d.err, d.wait_limit)) return;
-        // ---- exclusive scan: chunk totals, then each block scans its chunk ----
-        {
+        // ---- exclusive scan.  Small grids (at most 64 counts per thread): every
+        // block sums the counts before its chunk and all of them itself, with no
+        // grid-wide barrier.  Otherwise chunk totals first, then each block scans
+        // its chunk ----
+        const bool one_stage = nC <= 64 * NT;
+        if (!one_stage) {
             int sum = 0;
             for (int c = lo + threadIdx.x; c < hi; c += NT) sum += cnt[c];
             int total;
             block_excl_scan<NT>(sum, tmp, total);
             if (threadIdx.x == 0) gb.scan_tot[blockIdx.x] = total;
+            if (!grid_sync(gb, bar_target, d.err, d.wait_limit)) return;
         }
-        if (!grid_sync(gb, bar_target, d.err, d.wait_limit)) return;
         {
             int off = 0, all = 0;
-            for (int b = threadIdx.x; b < (int)gridDim.x; b += NT) {
-                const int v = gb.scan_tot[b];
-                all += v;
-                if (b < (int)blockIdx.x) off += v;
+            if (one_stage) {
+                for (int c = threadIdx.x; c < nC; c += NT) {
+                    const int v = cnt[c];
+                    all += v;
+                    if (c < lo) off += v;
+                }
+            } else {
+                for (int b = threadIdx.x; b < (int)gridDim.x; b += NT) {
+                    const int v = gb.scan_tot[b];
+                    all += v;
+                    if (b < (int)blockIdx.x) off += v;
+                }
             }
             int t1, t2;
             block_excl_scan<NT>(off, tmp, t1);
@@ -1791,11 +1816,16 @@ __global__ void __launch_bounds__(block_threads<W>(), W == 1 ? 3 : 1) sweep_pers
             // variant of the kernel, at 64000 molecules)
             for (int c = blockIdx.x * (NT / 32) + warp; c < nC; c += gridDim.x * (NT / 32))
                 cl_order_cell(d, buf ^ 1, c, lane);
+            if (!grid_sync(gb, bar_target, d.err, d.wait_limit)) return;
         } else {
-            for (int c = 4 * (blockIdx.x * (NT / 32) + warp); c < nC; c += 4 * gridDim.x * (NT / 32))
+            // (each ordered cell is published in cell_done: no grid-wide
+            // barrier before the colours)
+            for (int c = 4 * (blockIdx.x * (NT / 32) + warp); c < nC; c += 4 * gridDim.x * (NT / 32)) {
                 cl_order_cells4(d, buf ^ 1, c, lane);
+                __syncwarp();
+                if (lane < 4 && c + lane < nC) signal_done(d.cell_done + c + lane);
+            }
         }
-        if (!grid_sync(gb, bar_target, d.err, d.wait_limit)) return;
         // ---- the 8 colours, ordered cell by cell (no grid-wide barrier between
         // colours: each cell waits for its neighbours of smaller colours) ----
         for (int colour = 0; colour < 8; ++colour)
