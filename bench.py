@@ -64,8 +64,9 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 oracle-match-mode leg")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--autotune", type=int, default=4,
-                    help="sweeps per schedule for mc_autotune when the schedule is automatic (0: off)")
+    ap.add_argument("--autotune", type=int, default=-1,
+                    help="sweeps per schedule for mc_autotune when the schedule is automatic (0: off; -1: the "
+                         "sweeps of one timed step, so that each trial is one launch of the shape timed)")
     ap.add_argument("--one-by-one", type=int, default=16,
                     help="batched workloads: replicas timed one by one on their own handles (0: off)")
     ap.add_argument("--md", type=int, default=0,
@@ -484,11 +485,12 @@ def run_native(args):
                  launch_mode=args.launch_mode, warps_per_cell=args.warps_per_cell, recheck_gap=args.recheck_gap)
     N = h.N
     tuned = None
-    if args.autotune > 0 and args.warps_per_cell == 0 and args.launch_mode == 0:
+    trial = sps if args.autotune < 0 else args.autotune
+    if trial > 0 and args.warps_per_cell == 0 and args.launch_mode == 0:
         # pick the cell schedule on a copy of the state (the chain is unchanged)
-        res = h.autotune(args.autotune, wl["T"], mix, wl["seeds"])
+        res = h.autotune(trial, wl["T"], mix, wl["seeds"])
         tuned = {"ms_per_sweep": {"persistent": [float(x) for x in res[:4]], "graphs": [float(x) for x in res[4:]]},
-                 "warps_per_cell": [1, 2, 4, 8], "sweeps_per_trial": args.autotune}
+                 "warps_per_cell": [1, 2, 4, 8], "sweeps_per_trial": trial}
     # a dedicated stream: the library enqueues on it, the events are recorded on it
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
@@ -557,7 +559,7 @@ def run_native(args):
     # FP64 oracle-match mode on the same workload
     fp64 = None
     if precision == "fp32" and not args.no_fp64:
-        fp64, (ms64, att64) = run_fp64_leg(F, wl, mix, sps, args.steps, args.warmup, args.autotune, stream, flush,
+        fp64, (ms64, att64) = run_fp64_leg(F, wl, mix, sps, args.steps, args.warmup, trial, stream, flush,
                                            sms)
         ms64_max, att64_all, _ = combine_ranks(ms64, att64, 0, dist, "cuda")
         fp64["value"] = att64_all / (ms64_max / 1000.0)
