@@ -121,7 +121,7 @@ struct mc_handle {
     MixDev *d_mix = nullptr;
     int *d_rep_of_site = nullptr;
     int *d_act_off = nullptr;
-    int *d_rep_of_act = nullptr;
+    int2 *d_act_slot = nullptr;
     double *d_e_site = nullptr;          // per-cell (or per-site) FP64 partial sums
     double *d_e_out = nullptr;
     long long *d_X = nullptr;
@@ -452,7 +452,8 @@ int create_impl(mc_handle **out, int n_rep, const double *L, const int32_t *n_mo
     // layout
     long long sites = 0, cells = 0, act = 0;
     double max_stencil = 0.0;
-    std::vector<int> act_off(n_rep + 1, 0), rep_of_site, rep_of_act;
+    std::vector<int> act_off(n_rep + 1, 0), rep_of_site;
+    std::vector<double> cell_load(n_rep, 0.0);
     for (int r = 0; r < n_rep; ++r) {
         if (n_mol[r] < 1 || n_mol[r] > kMaxMolecules) {
             delete h;
@@ -499,7 +500,7 @@ int create_impl(mc_handle **out, int n_rep, const double *L, const int32_t *n_mo
         cells += (long long)nc * nc * nc;
         act += (long long)(nc / 2) * (nc / 2) * (nc / 2);
         act_off[r + 1] = (int)act;
-        rep_of_act.resize(act, r);
+        cell_load[r] = (double)ri.n_sites / ((double)nc * nc * nc);
         // neighbourhood size: mean plus six standard deviations
         // (counts are at most Poisson-distributed in a liquid) and a margin
         const double per_cell = (double)ri.n_sites / ((double)nc * nc * nc);
@@ -514,6 +515,19 @@ int create_impl(mc_handle **out, int n_rep, const double *L, const int32_t *n_mo
     h->n_sites = (int)sites;
     h->n_cells = (int)cells;
     h->n_act = (int)act;
+    // active-cell slots in schedule order: replicas with the most atoms per
+    // cell first (a cell's phase costs about its atoms times its neighbourhood,
+    // so the dense replicas' cells go in the first waves of a phase launch and
+    // the light ones fill its tail); within a replica, active-cell order
+    std::vector<int2> act_slot;
+    if (n_rep > 1) {
+        std::vector<int> order(n_rep);
+        for (int r = 0; r < n_rep; ++r) order[r] = r;
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cell_load[a] > cell_load[b]; });
+        act_slot.reserve((size_t)act);
+        for (int r : order)
+            for (int a = 0; a < act_off[r + 1] - act_off[r]; ++a) act_slot.push_back(make_int2(r, a));
+    }
     // staging capacity: the neighbourhood (mean + 6 sigma + 32) plus the padding records, a multiple of 32
     int cap = o.stencil_cap > 0 ? o.stencil_cap : ((int)std::ceil(max_stencil) + kPadSlots + 31) / 32 * 32;
     h->stencil_cap = cap;
@@ -559,7 +573,7 @@ int create_impl(mc_handle **out, int n_rep, const double *L, const int32_t *n_mo
     if ((rc = h->alloc(&h->d_rep, n_rep)) || (rc = h->alloc(&h->d_par, n_rep)) || (rc = h->alloc(&h->d_ctr, n_rep)) ||
         (rc = h->alloc(&h->d_model, 1)) || (rc = h->alloc(&h->d_mix, 1)) ||
         (rc = h->alloc(&h->d_rep_of_site, h->n_sites)) || (rc = h->alloc(&h->d_act_off, n_rep + 1)) ||
-        (rc = h->alloc(&h->d_rep_of_act, h->n_act)) ||
+        (rc = h->alloc(&h->d_act_slot, n_rep > 1 ? h->n_act : 0)) ||
         (rc = h->alloc(&r0, h->n_sites)) || (rc = h->alloc(&r1, h->n_sites)) || (rc = h->alloc(&cc, h->n_cells)) ||
         (rc = h->alloc(&cs, h->n_cells + 1)) || (rc = h->alloc(&co, h->n_sites)) || (rc = h->alloc(&so, h->n_sites)) ||
         (rc = h->alloc(&img, 3 * (size_t)h->n_sites)) || (rc = h->alloc(&cde, h->n_cells)) ||
@@ -587,7 +601,7 @@ int create_impl(mc_handle **out, int n_rep, const double *L, const int32_t *n_mo
     d.mix = h->d_mix;
     d.rep_of_site = h->d_rep_of_site;
     d.act_off = h->d_act_off;
-    d.rep_of_act = h->d_rep_of_act;
+    d.act_slot = n_rep > 1 ? h->d_act_slot : nullptr;
     d.rec[0] = r0;
     d.rec[1] = r1;
     d.cell_count = cc;
@@ -607,7 +621,7 @@ int create_impl(mc_handle **out, int n_rep, const double *L, const int32_t *n_mo
     if (!up(h->d_rep, h->reps.data(), sizeof(RepInfo) * n_rep) || !up(h->d_model, &h->model_host, sizeof(ModelDev)) ||
         !up(h->d_rep_of_site, rep_of_site.data(), sizeof(int) * h->n_sites) ||
         !up(h->d_act_off, act_off.data(), sizeof(int) * (n_rep + 1)) ||
-        !up(h->d_rep_of_act, rep_of_act.data(), sizeof(int) * h->n_act) ||
+        (n_rep > 1 && !up(h->d_act_slot, act_slot.data(), sizeof(int2) * h->n_act)) ||
         !up(h->d_par, h->par_host.data(), sizeof(RepParam) * n_rep)) {
         mc_destroy(h);
         return fail(MC_ERR_CUDA, "upload of tables failed");

@@ -101,7 +101,8 @@ struct DevState {
     const MixDev *mix;
     const int *rep_of_site;
     const int *act_off;  // n_rep + 1 prefix of (nc/2)^3
-    const int *rep_of_act;   // per active-cell slot of a colour (n_act): its replica
+    const int2 *act_slot;    // per active-cell slot of a colour (n_act), in schedule order: {replica, active
+                             // cell within the replica}; null for one replica (slot = active cell)
     int4 *rec[2];        // double-buffered records {qx, qy, qz, w}, cell-sorted
     int *cell_count;
     int *cell_count2;    // second count buffer (persistent launch: sweep s + 1 is counted while sweep s finishes)

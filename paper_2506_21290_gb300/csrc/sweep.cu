@@ -1281,12 +1281,13 @@ __device__ void run_cell(const DevState &d, int buf, int colour, const LogArgs &
     const WarpScr S = warp_scr(G, wig);
 
     // ---- which cell ----
-    const int r = d.n_rep == 1 ? 0 : d.rep_of_act[g];
+    const int2 sl = d.act_slot ? d.act_slot[g] : make_int2(0, g);
+    const int r = sl.x;
     const RepInfo ri = d.rep[r];
     const RepParam dy = d.par[r];
     const RepCtr ct = d.ctr[r];
     const int nc = ri.nc, h2 = nc >> 1;
-    const int a_loc = g - ri.act_off;
+    const int a_loc = sl.y;
     const int cx = 2 * (a_loc % h2) + (colour & 1);
     const int cy = 2 * ((a_loc / h2) % h2) + ((colour >> 1) & 1);
     const int cz = 2 * (a_loc / (h2 * h2)) + ((colour >> 2) & 1);
@@ -1598,13 +1599,19 @@ __device__ void run_cell(const DevState &d, int buf, int colour, const LogArgs &
     }
 }
 
+// threads per block of the phase kernel: one-warp groups get a block each, so
+// that a warp that finishes its cell frees its place at once (with four cells
+// per block the block held its place until its slowest cell was done)
+template <int W>
+__host__ __device__ constexpr int phase_threads() { return W == 1 ? 32 : block_threads<W>(); }
+
 // One colour phase, one launch: group g of the grid owns active cell g.
-// W = 1 serves large grids (many cells per SM): registers for three resident blocks
+// W = 1 serves large grids (many cells per SM): registers for fifteen resident blocks (128 per thread)
 template <int PREC, int W>
-__global__ void __launch_bounds__(block_threads<W>(), W == 1 ? 3 : 1) phase_kernel(DevState d, int buf, int colour,
+__global__ void __launch_bounds__(phase_threads<W>(), W == 1 ? 15 : 1) phase_kernel(DevState d, int buf, int colour,
                                                                                  LogArgs lg)
 {
-    constexpr int CPB = block_threads<W>() / (32 * W);
+    constexpr int CPB = phase_threads<W>() / (32 * W);
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ ModelDev md;
     __shared__ MixDev mx;
@@ -1901,15 +1908,16 @@ int phase_set_smem_limit(int bytes_needed)
 template <int PREC>
 static void launch_prec(const DevState &d, int buf, int W, const LogArgs &lg, cudaStream_t st)
 {
-    const int nt = W > 4 ? 32 * W : BLOCK;
+    const int nt = W == 8 ? phase_threads<8>() : W == 4 ? phase_threads<4>() : W == 2 ? phase_threads<2>()
+                                                                                  : phase_threads<1>();
     const int cpb = nt / (32 * W);
     const int blocks = (d.n_act + cpb - 1) / cpb;
-    const size_t sm = phase_smem_bytes(d.stencil_cap, W);
+    const size_t sm = group_bytes(d.stencil_cap, W) * (size_t)cpb;
     for (int colour = 0; colour < 8; ++colour) {
-        if (W == 8) phase_kernel<PREC, 8><<<blocks, 256, sm, st>>>(d, buf, colour, lg);
-        else if (W == 4) phase_kernel<PREC, 4><<<blocks, BLOCK, sm, st>>>(d, buf, colour, lg);
-        else if (W == 2) phase_kernel<PREC, 2><<<blocks, BLOCK, sm, st>>>(d, buf, colour, lg);
-        else phase_kernel<PREC, 1><<<blocks, BLOCK, sm, st>>>(d, buf, colour, lg);
+        if (W == 8) phase_kernel<PREC, 8><<<blocks, nt, sm, st>>>(d, buf, colour, lg);
+        else if (W == 4) phase_kernel<PREC, 4><<<blocks, nt, sm, st>>>(d, buf, colour, lg);
+        else if (W == 2) phase_kernel<PREC, 2><<<blocks, nt, sm, st>>>(d, buf, colour, lg);
+        else phase_kernel<PREC, 1><<<blocks, nt, sm, st>>>(d, buf, colour, lg);
     }
 }
 
