@@ -55,7 +55,7 @@ namespace flipmc {
 
 constexpr int TERM_CAP = 128;       // nonzero FP64 terms of one move
 constexpr int QW = 64;              // interaction queue entries per warp
-constexpr int BLOCK = 128;          // threads per block for W <= 4 (and of the per-replica sums)
+constexpr int BLOCK = 128;          // threads per block for W = 2, 4 and the persistent W = 1 kernel (and the per-replica sums)
 
 // threads per block of the sweep kernels: BLOCK, or one group of W warps when W > 4
 template <int W>
