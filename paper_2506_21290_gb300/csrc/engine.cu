@@ -16,6 +16,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/flipmc.h"
@@ -65,6 +66,28 @@ struct Buf {
 // mc_test_fail_alloc: allocations left before the one that fails (-1: off)
 std::atomic<int> g_fail_alloc{-1};
 
+// f(begin, end) over [0, n) in contiguous chunks of at least `grain` items, on
+// up to 16 host threads (the calling thread takes the first chunk); returns
+// when every chunk is done
+template <class F>
+void host_parallel(size_t n, size_t grain, const F &f)
+{
+    const unsigned hw = std::thread::hardware_concurrency();
+    const size_t nt = std::min<size_t>(std::min<size_t>(hw ? hw : 1, 16), (n + grain - 1) / std::max<size_t>(grain, 1));
+    if (nt <= 1) {
+        f((size_t)0, n);
+        return;
+    }
+    const size_t chunk = (n + nt - 1) / nt;
+    std::vector<std::thread> th;
+    for (size_t t = 1; t < nt; ++t) {
+        const size_t b = t * chunk, e = std::min(n, b + chunk);
+        if (b < e) th.emplace_back([&f, b, e] { f(b, e); });
+    }
+    f((size_t)0, std::min(n, chunk));
+    for (auto &x : th) x.join();
+}
+
 }  // namespace
 
 struct mc_handle {
@@ -86,7 +109,28 @@ struct mc_handle {
     double *d_drift = nullptr;           // per replica: last and largest relative drift
     mc_params params{};
     std::vector<RepInfo> reps;
-    std::vector<int> mol_off;
+    // page-locked host staging of the state's uploads and downloads, grown on
+    // demand (pageable memory when page-locked memory cannot be had)
+    void *pin = nullptr;
+    size_t pin_bytes = 0;
+    std::vector<unsigned char> pageable;
+    void *host_buf(size_t bytes)
+    {
+        if (pin && pin_bytes >= bytes) return pin;
+        if (pin) {
+            cudaFreeHost(pin);
+            pin = nullptr;
+            pin_bytes = 0;
+        }
+        if (cudaHostAlloc(&pin, bytes, cudaHostAllocDefault) == cudaSuccess) {
+            pin_bytes = bytes;
+            return pin;
+        }
+        pin = nullptr;
+        cudaGetLastError();
+        pageable.resize(bytes);
+        return pageable.data();
+    }
     cudaStream_t own_stream = nullptr;
     cudaStream_t stream = nullptr;
     int cur = 0;
@@ -274,33 +318,59 @@ int32_t fixed_half_width(double d, double L)
 }
 
 // Quantise (xyz) or take as given (qfix) and pack the records of all replicas
-// (site order); validate bonds.
-int pack_records(mc_handle *h, const double *xyz, const uint32_t *qfix, const int32_t *types, std::vector<int4> &rec)
+// (site order) into rec (n_sites entries); validate types, positions and
+// bonds.  Host threads take contiguous runs of molecules.  The error reported
+// is the one the serial order meets first (replicas in order; within a
+// replica every site, in order, before any bond), whichever thread finds it:
+// each error has a key (replica, site or bond, index, kind) and the smallest
+// key wins.
+int pack_records(mc_handle *h, const double *xyz, const uint32_t *qfix, const int32_t *types, int4 *rec)
 {
-    rec.resize(h->n_sites);
-    for (int r = 0; r < h->n_rep; ++r) {
-        const RepInfo &ri = h->reps[r];
-        for (int i = 0; i < ri.n_sites; ++i) {
-            const int g = ri.site_off + i;
-            const int t = types[g];
-            if (t < 0 || t > 2) return fail(MC_ERR_INVALID_ARG, "type outside {0,1,2}");
-            int4 v;
-            if (qfix) {
-                v.x = (int)qfix[3 * (size_t)g + 0];
-                v.y = (int)qfix[3 * (size_t)g + 1];
-                v.z = (int)qfix[3 * (size_t)g + 2];
-            } else {
-                for (int ax = 0; ax < 3; ++ax)
-                    if (!std::isfinite(xyz[3 * (size_t)g + ax])) return fail(MC_ERR_BAD_STATE, "non-finite position");
-                v.x = (int)quantize(xyz[3 * (size_t)g + 0], ri.L);
-                v.y = (int)quantize(xyz[3 * (size_t)g + 1], ri.L);
-                v.z = (int)quantize(xyz[3 * (size_t)g + 2], ri.L);
+    constexpr uint64_t kNone = ~0ull;
+    enum { kType = 0, kFinite = 1 };
+    auto site_key = [](int r, int i, int kind) { return ((uint64_t)r << 36) | ((uint64_t)i << 1) | (uint64_t)kind; };
+    auto bond_key = [](int r, int m) { return ((uint64_t)r << 36) | (1ull << 35) | ((uint64_t)m << 1); };
+    std::atomic<uint64_t> first{kNone};
+    const size_t nmol = (size_t)h->n_sites / 3;
+    host_parallel(nmol, 8192, [&](size_t mb, size_t me) {
+        uint64_t low = kNone;
+        int r = (int)(std::upper_bound(h->reps.begin(), h->reps.end(), mb,
+                                       [](size_t m, const RepInfo &ri) { return m < (size_t)ri.site_off / 3; }) -
+                      h->reps.begin()) - 1;
+        for (size_t M = mb; M < me; ++M) {
+            while ((size_t)(h->reps[r].site_off + h->reps[r].n_sites) / 3 <= M) ++r;
+            const RepInfo &ri = h->reps[r];
+            const int m = (int)(M - (size_t)ri.site_off / 3);
+            bool ok = true;
+            for (int k = 0; k < 3; ++k) {
+                const int i = 3 * m + k;
+                const size_t g = (size_t)ri.site_off + i;
+                const int t = types[g];
+                int4 v = make_int4(0, 0, 0, 0);
+                uint64_t key = kNone;
+                if (t < 0 || t > 2) {
+                    key = site_key(r, i, kType);
+                } else if (qfix) {
+                    v.x = (int)qfix[3 * g + 0];
+                    v.y = (int)qfix[3 * g + 1];
+                    v.z = (int)qfix[3 * g + 2];
+                } else if (!std::isfinite(xyz[3 * g + 0]) || !std::isfinite(xyz[3 * g + 1]) ||
+                           !std::isfinite(xyz[3 * g + 2])) {
+                    key = site_key(r, i, kFinite);
+                } else {
+                    v.x = (int)quantize(xyz[3 * g + 0], ri.L);
+                    v.y = (int)quantize(xyz[3 * g + 1], ri.L);
+                    v.z = (int)quantize(xyz[3 * g + 2], ri.L);
+                }
+                v.w = (m << 4) | (k << 2) | (t & 3);
+                rec[g] = v;
+                if (key != kNone) {
+                    ok = false;
+                    low = std::min<uint64_t>(low, key);
+                }
             }
-            v.w = ((i / 3) << 4) | ((i % 3) << 2) | t;
-            rec[g] = v;
-        }
-        // every bond strictly inside its FENE range
-        for (int m = 0; m < ri.n_sites / 3; ++m)
+            if (!ok) continue;
+            // every bond strictly inside its FENE range
             for (int k = 0; k < 3; ++k)
                 for (int l = k + 1; l < 3; ++l) {
                     const int4 a = rec[ri.site_off + 3 * m + k], b = rec[ri.site_off + 3 * m + l];
@@ -311,12 +381,21 @@ int pack_records(mc_handle *h, const double *xyz, const uint32_t *qfix, const in
                         const double x = (double)da[ax] * ri.h;
                         r2 += x * x;
                     }
-                    if (!(r2 < h->model_host.R2[3 * (a.w & 3) + (b.w & 3)]))
-                        return fail(MC_ERR_BAD_STATE, "a bond is at or beyond its FENE range (replica " +
-                                                          std::to_string(r) + ", molecule " + std::to_string(m) + ")");
+                    if (!(r2 < h->model_host.R2[3 * (a.w & 3) + (b.w & 3)])) low = std::min<uint64_t>(low, bond_key(r, m));
                 }
-    }
-    return MC_OK;
+        }
+        uint64_t cur = first.load();
+        while (low < cur && !first.compare_exchange_weak(cur, low)) {
+        }
+    });
+    const uint64_t key = first.load();
+    if (key == kNone) return MC_OK;
+    const int r = (int)(key >> 36);
+    if ((key >> 35) & 1)
+        return fail(MC_ERR_BAD_STATE, "a bond is at or beyond its FENE range (replica " + std::to_string(r) +
+                                          ", molecule " + std::to_string((int)((key >> 1) & 0x3FFFFFFFull)) + ")");
+    if ((key & 1) == kType) return fail(MC_ERR_INVALID_ARG, "type outside {0,1,2}");
+    return fail(MC_ERR_BAD_STATE, "non-finite position");
 }
 
 int check_device_errors(mc_handle *h)
@@ -338,11 +417,11 @@ int enqueue_energy(mc_handle *h)
     return MC_OK;
 }
 
-int rebuild_and_reset(mc_handle *h, const std::vector<int4> &rec, const std::vector<int> *img = nullptr)
+int rebuild_and_reset(mc_handle *h, const int4 *rec, const std::vector<int> *img = nullptr)
 {
     // upload in site order into the spare buffer, sort into the other
     const int spare = h->cur;
-    CUDA_TRY(cudaMemcpyAsync(h->ds.rec[spare], rec.data(), sizeof(int4) * rec.size(), cudaMemcpyHostToDevice,
+    CUDA_TRY(cudaMemcpyAsync(h->ds.rec[spare], rec, sizeof(int4) * (size_t)h->n_sites, cudaMemcpyHostToDevice,
                              h->stream));
     launch_cell_list(h->ds, spare, spare ^ 1, h->stream);
     h->cur = spare ^ 1;
@@ -636,7 +715,7 @@ int create_impl(mc_handle **out, int n_rep, const double *L, const int32_t *n_mo
         mc_destroy(h);
         return fail(MC_ERR_INVALID_ARG, "persistent sweeps need cooperative launch support");
     }
-    std::vector<int4> rec;
+    int4 *rec = (int4 *)h->host_buf(sizeof(int4) * (size_t)h->n_sites);
     rc = pack_records(h, xyz, nullptr, types, rec);
     if (rc == MC_OK) rc = rebuild_and_reset(h, rec);
     if (rc) {
@@ -693,6 +772,7 @@ void mc_destroy(mc_handle *h)
     for (int b = 0; b < 2; ++b)
         if (h->graph[b]) cudaGraphExecDestroy(h->graph[b]);
     for (auto &a : h->allocs) cudaFree(a.p);
+    if (h->pin) cudaFreeHost(h->pin);
     if (h->own_stream) cudaStreamDestroy(h->own_stream);
     delete h;
 }
@@ -1056,15 +1136,19 @@ int mc_pair_histogram(mc_handle *h, double dr, int n_bins, uint64_t *counts, dou
     return check_device_errors(h);
 }
 
-static int fetch_records(mc_handle *h, std::vector<int4> &rec, std::vector<int> &img)
+// the records (cell order) and, when img is asked for, the image counts (site
+// order), into the handle's host staging
+static int fetch_records(mc_handle *h, const int4 **rec, const int **img)
 {
-    rec.resize(h->n_sites);
-    img.resize(3 * (size_t)h->n_sites);
-    CUDA_TRY(cudaMemcpyAsync(rec.data(), h->ds.rec[h->cur], sizeof(int4) * h->n_sites, cudaMemcpyDeviceToHost,
-                             h->stream));
-    CUDA_TRY(cudaMemcpyAsync(img.data(), h->ds.img, sizeof(int) * 3 * (size_t)h->n_sites, cudaMemcpyDeviceToHost,
-                             h->stream));
+    const size_t n = (size_t)h->n_sites;
+    unsigned char *buf = (unsigned char *)h->host_buf(sizeof(int4) * n + (img ? sizeof(int) * 3 * n : 0));
+    CUDA_TRY(cudaMemcpyAsync(buf, h->ds.rec[h->cur], sizeof(int4) * n, cudaMemcpyDeviceToHost, h->stream));
+    if (img)
+        CUDA_TRY(cudaMemcpyAsync(buf + sizeof(int4) * n, h->ds.img, sizeof(int) * 3 * n, cudaMemcpyDeviceToHost,
+                                 h->stream));
     CUDA_TRY(cudaStreamSynchronize(h->stream));
+    *rec = (const int4 *)buf;
+    if (img) *img = (const int *)(buf + sizeof(int4) * n);
     return check_device_errors(h);
 }
 
@@ -1079,13 +1163,18 @@ int mc_state(mc_handle *h, double *xyz_out, int32_t *types_out, mc_stats *stats_
     int rc = set_device(h);
     if (rc) return rc;
     if (xyz_out || types_out) {
-        std::vector<int4> rec;
-        std::vector<int> img;
-        if ((rc = fetch_records(h, rec, img))) return rc;
-        for (int r = 0; r < h->n_rep; ++r) {
-            const RepInfo &ri = h->reps[r];
-            for (int i = 0; i < ri.n_sites; ++i) {
-                const int4 v = rec[ri.site_off + i];
+        const int4 *rec = nullptr;
+        if ((rc = fetch_records(h, &rec, nullptr))) return rc;
+        // on host threads, each taking a run of record slots (a replica's
+        // records fill the slots of its sites; each record writes its own site)
+        host_parallel((size_t)h->n_sites, 65536, [&](size_t b, size_t e) {
+            int r = (int)(std::upper_bound(h->reps.begin(), h->reps.end(), b,
+                                           [](size_t g, const RepInfo &ri) { return g < (size_t)ri.site_off; }) -
+                          h->reps.begin()) - 1;
+            for (size_t g = b; g < e; ++g) {
+                while ((size_t)(h->reps[r].site_off + h->reps[r].n_sites) <= g) ++r;
+                const RepInfo &ri = h->reps[r];
+                const int4 v = rec[g];
                 const int s = site_of(h, r, v);
                 if (xyz_out) {
                     xyz_out[3 * (size_t)s + 0] = (double)(uint32_t)v.x * ri.h;
@@ -1094,7 +1183,7 @@ int mc_state(mc_handle *h, double *xyz_out, int32_t *types_out, mc_stats *stats_
                 }
                 if (types_out) types_out[s] = v.w & 3;
             }
-        }
+        });
     }
     if (stats_out) {
         std::vector<unsigned long long> st((size_t)STAT_N * h->n_rep);
@@ -1132,9 +1221,9 @@ int mc_state_fixed(mc_handle *h, uint32_t *q_out, int64_t *X_out, int32_t *types
     if (!h) return fail(MC_ERR_INVALID_ARG, "NULL handle");
     int rc = set_device(h);
     if (rc) return rc;
-    std::vector<int4> rec;
-    std::vector<int> img;
-    if ((rc = fetch_records(h, rec, img))) return rc;
+    const int4 *rec = nullptr;
+    const int *img = nullptr;
+    if ((rc = fetch_records(h, &rec, &img))) return rc;
     for (int r = 0; r < h->n_rep; ++r) {
         const RepInfo &ri = h->reps[r];
         for (int i = 0; i < ri.n_sites; ++i) {
@@ -1156,7 +1245,7 @@ int mc_set_state(mc_handle *h, const double *xyz, const int32_t *types)
     if (!h || !xyz || !types) return fail(MC_ERR_INVALID_ARG, "NULL argument");
     int rc = set_device(h);
     if (rc) return rc;
-    std::vector<int4> rec;
+    int4 *rec = (int4 *)h->host_buf(sizeof(int4) * (size_t)h->n_sites);
     if ((rc = pack_records(h, xyz, nullptr, types, rec))) return rc;
     return rebuild_and_reset(h, rec);
 }
@@ -1166,7 +1255,7 @@ int mc_set_state_fixed(mc_handle *h, const uint32_t *q, const int64_t *X, const 
     if (!h || !q || !types) return fail(MC_ERR_INVALID_ARG, "NULL argument");
     int rc = set_device(h);
     if (rc) return rc;
-    std::vector<int4> rec;
+    int4 *rec = (int4 *)h->host_buf(sizeof(int4) * (size_t)h->n_sites);
     if ((rc = pack_records(h, nullptr, q, types, rec))) return rc;
     if (!X) return rebuild_and_reset(h, rec);
     std::vector<int> img(3 * (size_t)h->n_sites);
