@@ -192,7 +192,12 @@ typedef struct {
  * params/opts: NULL picks the paper's potential and FP32 defaults.
  * Errors: INVALID_ARG (sizes, types, box smaller than two cells of side
  * R0*max sigma), BAD_STATE (a bond at or beyond R0 sigma_ab, or a non-finite
- * energy), NO_DEVICE, CUDA.  Model: Sec. II.A; schedule as described above.
+ * energy), NO_DEVICE, CUDA; of several invalid inputs the one met first in
+ * replica, then site, then bond order is reported.  Host work: the packing and
+ * validation of more than 8192 molecules runs on up to 16 host threads started
+ * and joined inside the call; the handle keeps a page-locked staging buffer
+ * (16 to 28 bytes per atom) for the state's copies.  Model: Sec. II.A; schedule as
+ * described above.
  */
 int mc_create(mc_handle **out, double L, int n_mol, const double *xyz, const int32_t *types,
               const mc_params *params, const mc_options *opts);
@@ -308,7 +313,8 @@ int mc_sweep_timed(mc_handle *h, int n_sweeps, const double *T, const mc_move_mi
 /*
  * Copy the state out: xyz_out[3*total_sites] (wrapped, x = q L / 2^32),
  * types_out[total_sites], stats_out[n_rep]; any pointer may be NULL.
- * Synchronous.
+ * Synchronous; more than 65536 atoms are converted on up to 16 host threads
+ * started and joined inside the call.
  */
 int mc_state(mc_handle *h, double *xyz_out, int32_t *types_out, mc_stats *stats_out);
 
