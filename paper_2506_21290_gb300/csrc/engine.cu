@@ -67,8 +67,8 @@ struct Buf {
 std::atomic<int> g_fail_alloc{-1};
 
 // f(begin, end) over [0, n) in contiguous chunks of at least `grain` items, on
-// up to 16 host threads (the calling thread takes the first chunk); returns
-// when every chunk is done
+// up to 16 host threads (the calling thread takes the first chunk, and any
+// chunk whose thread the system refuses); returns when every chunk is done
 template <class F>
 void host_parallel(size_t n, size_t grain, const F &f)
 {
@@ -82,7 +82,12 @@ void host_parallel(size_t n, size_t grain, const F &f)
     std::vector<std::thread> th;
     for (size_t t = 1; t < nt; ++t) {
         const size_t b = t * chunk, e = std::min(n, b + chunk);
-        if (b < e) th.emplace_back([&f, b, e] { f(b, e); });
+        if (b >= e) continue;
+        try {
+            th.emplace_back([&f, b, e] { f(b, e); });
+        } catch (...) {
+            f(b, e);
+        }
     }
     f((size_t)0, std::min(n, chunk));
     for (auto &x : th) x.join();

@@ -1146,7 +1146,7 @@ __device__ __forceinline__ unsigned tally_inc(const Res &R, int lane)
     inc += (lane == STAT_ACC + R.mvt) & (R.accept != 0);
     inc += (lane == STAT_REJ_GEOM) & geom;
     inc += (lane == STAT_REJ_BOND) & (R.status == MC_ST_BOND_BREAK);
-    inc += (lane == STAT_PAIRS) & evaluated ? (unsigned)R.pairs : 0u;
+    inc += ((lane == STAT_PAIRS) & evaluated) ? (unsigned)R.pairs : 0u;
     inc += (lane == STAT_RECHECK) ? (unsigned)R.flags : 0u;
     return inc;
 }
