@@ -44,7 +44,7 @@ L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) per launch of the dominant kernel, from one ncu
 # capture of that kernel on that workload; keyed by (workload, kernel, sweeps
 # per launch), so a timed launch that differs from the captured one reports null
-NCU_TRAFFIC = {("single-8000", "sweep_persistent<FP32,W=2>", 20): 666368 + 245248}
+NCU_TRAFFIC = {}
 
 
 def parse():
